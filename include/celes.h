@@ -1,0 +1,209 @@
+/*
+ * celes.h -- C ABI of the GB300 (sm_103a) multi-sphere T-matrix solver.
+ *
+ * The library solves the master equation of the multiple-scattering problem
+ * (CELES, JQSRT 2017, Sec. 2.2, Eqs. for a^i, M and the master equation):
+ *
+ *     sum_{i',n'} M^{ii'}_{nn'} b^{i'}_{n'} = sum_{n'} T^i_{nn'} a^i_{in,n'},
+ *     M^{ii'}_{nn'} = delta_{nn'} delta_{ii'} - sum_{n''} T^i_{nn''} W^{ii'}_{n''n'},
+ *     W^{ii'}_{nn'} = A_{n'n}(r_i - r_i')           (App. A.2 translation operator)
+ *
+ * with an iterative solver whose matrix-vector products evaluate the coupling
+ * blocks on the fly (Sec. 3.2).  All compute runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lengths in one user-chosen unit (the tests use nanometres); k0 = 2 pi /
+ *    lambda_vacuum in the inverse unit.  Background wavenumber k = n0 k0.
+ *  - Coefficient order per sphere (fixed by this library; the paper fixes
+ *    none): n = (tau-1) L(L+2) + l(l+1) - 1 + m, tau in {1,2}, l = 1..L,
+ *    m = -l..l; nmax = 2 L (L+2).
+ *  - Complex numbers are interleaved (re, im).  FP64 data are complex128,
+ *    FP32 data complex64.  Coefficient vectors are [nrhs][N][nmax].
+ *  - Host pointers are only read during the call; the library copies what it
+ *    keeps.  Device pointers passed to the *_matvec / *_apply calls belong to
+ *    the caller and must hold the stated number of elements on the context's
+ *    device; the library never frees them.
+ *  - stream: a cudaStream_t passed as void*; NULL means the context's own
+ *    stream.  Calls taking a stream are stream-ordered and do not synchronise.
+ *  - Every call returns a celes_status; on failure celes_last_error() gives a
+ *    one-line reason.  Invalid arguments return CELES_EINVAL before any GPU
+ *    work is queued.
+ */
+#ifndef CELES_H_
+#define CELES_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct celes_ctx celes_ctx;
+
+typedef enum {
+  CELES_OK = 0,
+  CELES_EINVAL = -1,    /* invalid argument */
+  CELES_ENOMEM = -2,    /* device allocation failed */
+  CELES_ECUDA = -3,     /* CUDA runtime error */
+  CELES_ENOCONV = -4,   /* solver stopped before the tolerance; best iterate kept */
+  CELES_ENUMERIC = -5,  /* NaN/Inf or breakdown detected */
+  CELES_EOVERLAP = -6,  /* two spheres overlap (|r_i - r_j| < R_i + R_j) */
+  CELES_ETIMEOUT = -7,  /* a bounded device wait gave up */
+  CELES_ESTATE = -8     /* call out of order (e.g. solve before set_incident) */
+} celes_status;
+
+typedef enum { CELES_FP64 = 0, CELES_FP32 = 1 } celes_precision;
+
+typedef struct {
+  int device;           /* CUDA device ordinal (default 0) */
+  int check_overlap;    /* reject overlapping spheres (default 1) */
+  int chunks;           /* source chunks of the coupling kernel; 0 = automatic */
+} celes_options;
+
+typedef enum { CELES_PLANE_WAVE = 0, CELES_GAUSSIAN_BEAM = 1 } celes_incident_kind;
+
+/* One incident field (one right-hand side).
+ *  Plane wave (App. A.1 PVWF): E = E0 Phi_pol(alpha, beta; r), pol 1 = along
+ *    e_alpha, 2 = along e_beta.  beta = 0, alpha = 0, pol = 2 is x-polarised
+ *    along +z.
+ *  Gaussian beam (App. C): waist w, focus r_G, polarisation
+ *    E0 (-sin alpha_G e_x + cos alpha_G e_y), angular spectrum restricted to
+ *    beta in [0, pi/2]; n_beta Gauss-Legendre nodes (0 = 128). */
+typedef struct {
+  int kind;
+  double beta, alpha;
+  int pol;
+  double E0_re, E0_im;
+  double waist;
+  double focus[3];
+  double alpha_G;
+  int n_beta;
+} celes_incident;
+
+typedef enum {
+  CELES_SOLVE_FP64 = 0,   /* plain FP64 GMRES, FP64 coupling matvec */
+  CELES_SOLVE_MIXED = 1   /* FP32 inner GMRES + FP64 residual refinement */
+} celes_solve_mode;
+
+typedef enum {
+  CELES_X0_TA = 0,     /* initial guess T a_in */
+  CELES_X0_USER = 1,   /* guess given by celes_set_initial_guess */
+  CELES_X0_ZERO = 2
+} celes_x0_kind;
+
+typedef struct {
+  int mode;             /* celes_solve_mode */
+  int restart;          /* GMRES restart length (default 100) */
+  int max_iter;         /* total inner iterations (default 2000) */
+  int max_outer;        /* refinement steps in MIXED mode (default 20) */
+  int x0;               /* celes_x0_kind */
+  int use_precond;      /* apply the block preconditioner if built (default 1) */
+  double inner_tol;     /* MIXED: relative tolerance floor of each FP32 solve (default 1e-5) */
+} celes_solve_opts;
+
+typedef struct {
+  int status;               /* celes_status of the solve */
+  int iterations;           /* total GMRES iterations (all precisions) */
+  int outer;                /* refinement steps (MIXED) or restarts (FP64) */
+  int matvecs_fp64;         /* coupling matvecs in FP64 */
+  int matvecs_fp32;         /* coupling matvecs in FP32 */
+  double residual;          /* final ||T a - M b|| / ||T a||, FP64, per RHS max */
+  double seconds;           /* wall time of the solve */
+  double* history;          /* optional caller buffer for the residual history */
+  int history_cap;          /* its capacity */
+  int history_len;          /* entries written */
+} celes_solve_info;
+
+/* Create a context: copies positions [N][3], radii [N] and the complex
+ * refractive indices n_i [N] (re, im pairs) to the device, validates them and
+ * computes the Mie T-matrix (App. B) in FP64 on the GPU.
+ * lmax in 1..5.  opt may be NULL (defaults).  On success *out owns all device
+ * memory of the problem; release it with celes_destroy. */
+int celes_create(celes_ctx** out, int64_t N, const double* positions, const double* radii, const double* n_i,
+                 double n0, double k0, int lmax, const celes_options* opt);
+
+/* Set nrhs incident fields (array of nrhs descriptors) and compute their
+ * coefficients a_in (App. A.2 PVWF->SVWF transform for plane waves, App. C
+ * beta quadrature for Gaussian beams) in FP64 on the GPU.  Resets any
+ * previous solution. */
+int celes_set_incident(celes_ctx* ctx, const celes_incident* inc, int nrhs);
+
+/* y = W x (Sec. 2.2, Sec. 3.2.2): y_i = sum_{j != i} W^{ij} x_j for nrhs
+ * vectors, blocks evaluated on the fly.  x, y: device pointers to
+ * [nrhs][N][nmax] complex128 (CELES_FP64) or complex64 (CELES_FP32); x and y
+ * must not overlap. */
+int celes_coupling_matvec(celes_ctx* ctx, const void* x, void* y, int nrhs, int precision, void* stream);
+
+/* y = M x = x - T (W x) (Sec. 2.2, Eq. for M): the coupling matvec with the
+ * T-matrix epilogue fused (Sec. 3.2.2).  Same layout rules as above. */
+int celes_master_matvec(celes_ctx* ctx, const void* x, void* y, int nrhs, int precision, void* stream);
+
+/* Build the block-diagonal preconditioner (Sec. 3.2.1): partition the
+ * spheres by cuboids of the given edge (grid anchored at the minimum corner of
+ * the centres' bounding box, cuboids ordered by (z, y, x) index), assemble
+ * each diagonal block of M in FP64 and LU-factor it with partial pivoting on
+ * the GPU.  Replaces any earlier preconditioner. */
+int celes_precond_build(celes_ctx* ctx, double cuboid_edge);
+
+/* y = P^{-1} x with P the block-diagonal part of M (Sec. 3.2.1, step 4):
+ * per block, solve L_j U_j y = P_j x.  Layout as for the matvecs; FP32
+ * vectors are solved with the FP64 factors.  x and y may be equal. */
+int celes_precond_apply(celes_ctx* ctx, const void* x, void* y, int nrhs, int precision, void* stream);
+
+/* Provide an initial guess b0 ([nrhs][N][nmax] complex128, host) used by
+ * celes_solve with x0 = CELES_X0_USER (Sec. 4.2, custom initial condition). */
+int celes_set_initial_guess(celes_ctx* ctx, const double* b0_host);
+
+/* Solve M b = T a_in for every RHS to ||T a - M b|| / ||T a|| <= tol
+ * (FP64 residual).  o and info may be NULL.  Returns CELES_ENOCONV if the
+ * iteration budget ran out (the best b is still stored). */
+int celes_solve(celes_ctx* ctx, double tol, const celes_solve_opts* o, celes_solve_info* info);
+
+/* Copy results to the host ([nrhs][N][nmax] complex128). */
+int celes_get_coefficients(celes_ctx* ctx, double* b_host);
+int celes_get_incident_coefficients(celes_ctx* ctx, double* a_host);
+/* T-matrix diagonal: [N][nmax] complex128 in coefficient order. */
+int celes_get_tmatrix(celes_ctx* ctx, double* t_host);
+
+/* Plane-wave amplitude of the scattered field of RHS `rhs` (App. D):
+ *   g_j(alpha, beta) = 1/(2 pi) sum_i e^{-i k.r_i} sum_n B_nj(beta) e^{i m alpha} b^i_n
+ * for Nd directions dirs [Nd][2] = (beta, alpha); writes g [Nd][2] complex128
+ * (host).  The radiant intensity is 2 pi^2/(omega k mu0) |g_j|^2. */
+int celes_farfield(celes_ctx* ctx, const double* dirs, int64_t Nd, double* g, int rhs);
+
+/* Problem sizes. */
+int64_t celes_num_spheres(const celes_ctx* ctx);
+int celes_nmax(const celes_ctx* ctx);
+int celes_num_rhs(const celes_ctx* ctx);
+
+/* Number of nonzero (a5, b5) terms of the coupling block built into the
+ * kernels for degree lmax (App. A.2), and their values: for every term t,
+ * idx[5t..5t+4] = (source row, receiving row, p, mu, kind) with rows
+ * r = l(l+1) - 1 + m, kind 0 = a5 (real) and 1 = b5/i (real), val[t] its
+ * real factor.  Host-only; pass NULL buffers to query the count.  Returns the
+ * count (>= 0) or CELES_EINVAL. */
+int celes_coupling_terms(int lmax, int* idx, double* val, int cap);
+
+/* Kernel timing with CUDA events recorded on the stream each kernel is
+ * launched on.  celes_profile(ctx, 1) starts recording (and clears earlier
+ * records), 0 stops.  celes_kernel_time(ctx, which, &ms, &launches)
+ * synchronises the context's stream and returns the summed duration and the
+ * launch count of one kernel class: which = 0 FP32 coupling kernel, 1 FP64
+ * coupling kernel, 2 coupling epilogue (both precisions).  The paper has no
+ * counterpart; this is measurement support. */
+int celes_profile(celes_ctx* ctx, int on);
+int celes_kernel_time(celes_ctx* ctx, int which, double* ms, int64_t* launches);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t celes_kernel_launches(void);
+
+void celes_destroy(celes_ctx* ctx);
+const char* celes_last_error(const celes_ctx* ctx);
+const char* celes_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELES_H_ */

@@ -1,0 +1,318 @@
+"""ctypes binding of the C ABI in ``include/celes.h`` (argument marshalling only).
+
+Every entry point of the C library has a Python function of the same name
+here.  Host arrays are NumPy arrays; device buffers for the matvec / apply
+calls are any objects exposing ``data_ptr()`` (torch CUDA tensors) or raw
+integer device addresses.  No arithmetic on problem data happens in Python:
+if the shared library is missing this module raises instead of falling back.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libceles_gb300.so")
+
+CELES_OK = 0
+CELES_EINVAL = -1
+CELES_ENOMEM = -2
+CELES_ECUDA = -3
+CELES_ENOCONV = -4
+CELES_ENUMERIC = -5
+CELES_EOVERLAP = -6
+CELES_ETIMEOUT = -7
+CELES_ESTATE = -8
+STATUS_NAMES = {0: "CELES_OK", -1: "CELES_EINVAL", -2: "CELES_ENOMEM", -3: "CELES_ECUDA", -4: "CELES_ENOCONV",
+                -5: "CELES_ENUMERIC", -6: "CELES_EOVERLAP", -7: "CELES_ETIMEOUT", -8: "CELES_ESTATE"}
+
+CELES_FP64 = 0
+CELES_FP32 = 1
+CELES_PLANE_WAVE = 0
+CELES_GAUSSIAN_BEAM = 1
+CELES_SOLVE_FP64 = 0
+CELES_SOLVE_MIXED = 1
+CELES_X0_TA = 0
+CELES_X0_USER = 1
+CELES_X0_ZERO = 2
+
+
+class celes_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("check_overlap", ctypes.c_int), ("chunks", ctypes.c_int)]
+
+
+class celes_incident(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("pol", ctypes.c_int), ("E0_re", ctypes.c_double), ("E0_im", ctypes.c_double),
+                ("waist", ctypes.c_double), ("focus", ctypes.c_double * 3), ("alpha_G", ctypes.c_double),
+                ("n_beta", ctypes.c_int)]
+
+
+class celes_solve_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("max_outer", ctypes.c_int), ("x0", ctypes.c_int), ("use_precond", ctypes.c_int),
+                ("inner_tol", ctypes.c_double)]
+
+
+class celes_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer", ctypes.c_int),
+                ("matvecs_fp64", ctypes.c_int), ("matvecs_fp32", ctypes.c_int), ("residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int)]
+
+
+_c_ctx_p = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+# (name, restype, argtypes) of every exported symbol of include/celes.h
+SIGNATURES = [
+    ("celes_create", ctypes.c_int, [ctypes.POINTER(_c_ctx_p), ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.POINTER(celes_options)]),
+    ("celes_set_incident", ctypes.c_int, [_c_ctx_p, ctypes.POINTER(celes_incident), ctypes.c_int]),
+    ("celes_coupling_matvec", ctypes.c_int, [_c_ctx_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_void_p]),
+    ("celes_master_matvec", ctypes.c_int, [_c_ctx_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_void_p]),
+    ("celes_precond_build", ctypes.c_int, [_c_ctx_p, ctypes.c_double]),
+    ("celes_precond_apply", ctypes.c_int, [_c_ctx_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_void_p]),
+    ("celes_set_initial_guess", ctypes.c_int, [_c_ctx_p, _dp]),
+    ("celes_solve", ctypes.c_int, [_c_ctx_p, ctypes.c_double, ctypes.POINTER(celes_solve_opts),
+                                   ctypes.POINTER(celes_solve_info)]),
+    ("celes_get_coefficients", ctypes.c_int, [_c_ctx_p, _dp]),
+    ("celes_get_incident_coefficients", ctypes.c_int, [_c_ctx_p, _dp]),
+    ("celes_get_tmatrix", ctypes.c_int, [_c_ctx_p, _dp]),
+    ("celes_farfield", ctypes.c_int, [_c_ctx_p, _dp, ctypes.c_int64, _dp, ctypes.c_int]),
+    ("celes_num_spheres", ctypes.c_int64, [_c_ctx_p]),
+    ("celes_nmax", ctypes.c_int, [_c_ctx_p]),
+    ("celes_num_rhs", ctypes.c_int, [_c_ctx_p]),
+    ("celes_coupling_terms", ctypes.c_int, [ctypes.c_int, _ip, _dp, ctypes.c_int]),
+    ("celes_profile", ctypes.c_int, [_c_ctx_p, ctypes.c_int]),
+    ("celes_kernel_time", ctypes.c_int, [_c_ctx_p, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    ("celes_kernel_launches", ctypes.c_int64, []),
+    ("celes_destroy", None, [_c_ctx_p]),
+    ("celes_last_error", ctypes.c_char_p, [_c_ctx_p]),
+    ("celes_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class CelesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, ctx=None):
+    if code != CELES_OK:
+        msg = ""
+        if ctx is not None:
+            m = load().celes_last_error(ctx)
+            msg = m.decode() if m else ""
+        raise CelesError(code, msg)
+    return code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _devptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# one Python function per C entry point
+# ---------------------------------------------------------------------------
+
+def celes_create(positions, radii, n_i, n0, k0, lmax, device=0, check_overlap=True, chunks=0):
+    pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1, 3)
+    rad = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    ni = np.ascontiguousarray(np.asarray(n_i, dtype=np.complex128).reshape(-1)).view(np.float64)
+    opt = celes_options(int(device), int(bool(check_overlap)), int(chunks))
+    ctx = _c_ctx_p()
+    code = load().celes_create(ctypes.byref(ctx), pos.shape[0], _dptr(pos), _dptr(rad), _dptr(ni),
+                               float(n0), float(k0), int(lmax), ctypes.byref(opt))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_create failed")
+    return ctx
+
+
+def make_incident(kind="plane", beta=0.0, alpha=0.0, pol=2, E0=1.0, waist=0.0, focus=(0.0, 0.0, 0.0),
+                  alpha_G=-np.pi / 2, n_beta=0):
+    d = celes_incident()
+    d.kind = CELES_PLANE_WAVE if kind == "plane" else CELES_GAUSSIAN_BEAM
+    d.beta, d.alpha, d.pol = float(beta), float(alpha), int(pol)
+    d.E0_re, d.E0_im = float(np.real(E0)), float(np.imag(E0))
+    d.waist = float(waist)
+    for q in range(3):
+        d.focus[q] = float(focus[q])
+    d.alpha_G = float(alpha_G)
+    d.n_beta = int(n_beta)
+    return d
+
+
+def celes_set_incident(ctx, incidents):
+    arr = (celes_incident * len(incidents))(*incidents)
+    return _check(load().celes_set_incident(ctx, arr, len(incidents)), ctx)
+
+
+def celes_coupling_matvec(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
+    return _check(load().celes_coupling_matvec(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
+                                               _stream(stream)), ctx)
+
+
+def celes_master_matvec(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
+    return _check(load().celes_master_matvec(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
+                                             _stream(stream)), ctx)
+
+
+def celes_precond_build(ctx, cuboid_edge):
+    return _check(load().celes_precond_build(ctx, float(cuboid_edge)), ctx)
+
+
+def celes_precond_apply(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
+    return _check(load().celes_precond_apply(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
+                                             _stream(stream)), ctx)
+
+
+def celes_set_initial_guess(ctx, b0):
+    b = np.ascontiguousarray(b0, dtype=np.complex128)
+    return _check(load().celes_set_initial_guess(ctx, _dptr(b.view(np.float64))), ctx)
+
+
+def celes_solve(ctx, tol, mode=CELES_SOLVE_MIXED, restart=100, max_iter=2000, max_outer=20, x0=CELES_X0_TA,
+                use_precond=True, inner_tol=1e-5, history_cap=4096, raise_on_noconv=True):
+    """Returns a dict with the solve statistics and the residual history."""
+    opts = celes_solve_opts(int(mode), int(restart), int(max_iter), int(max_outer), int(x0), int(bool(use_precond)),
+                            float(inner_tol))
+    hist = np.zeros(max(1, history_cap), dtype=np.float64)
+    info = celes_solve_info()
+    info.history = _dptr(hist)
+    info.history_cap = int(history_cap)
+    code = load().celes_solve(ctx, float(tol), ctypes.byref(opts), ctypes.byref(info))
+    out = {"status": int(code), "iterations": info.iterations, "outer": info.outer,
+           "matvecs_fp64": info.matvecs_fp64, "matvecs_fp32": info.matvecs_fp32, "residual": info.residual,
+           "seconds": info.seconds, "history": hist[:info.history_len].copy()}
+    if code != CELES_OK and not (code == CELES_ENOCONV and not raise_on_noconv):
+        _check(code, ctx)
+    return out
+
+
+def _host_vec(ctx, getter, shape):
+    out = np.zeros(shape, dtype=np.complex128)
+    _check(getter(ctx, _dptr(out.view(np.float64))), ctx)
+    return out
+
+
+def celes_get_coefficients(ctx):
+    lib = load()
+    return _host_vec(ctx, lib.celes_get_coefficients,
+                     (lib.celes_num_rhs(ctx), lib.celes_num_spheres(ctx), lib.celes_nmax(ctx)))
+
+
+def celes_get_incident_coefficients(ctx):
+    lib = load()
+    return _host_vec(ctx, lib.celes_get_incident_coefficients,
+                     (lib.celes_num_rhs(ctx), lib.celes_num_spheres(ctx), lib.celes_nmax(ctx)))
+
+
+def celes_get_tmatrix(ctx):
+    lib = load()
+    return _host_vec(ctx, lib.celes_get_tmatrix, (lib.celes_num_spheres(ctx), lib.celes_nmax(ctx)))
+
+
+def celes_farfield(ctx, dirs, rhs=0):
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 2)
+    g = np.zeros((d.shape[0], 2), dtype=np.complex128)
+    _check(load().celes_farfield(ctx, _dptr(d), d.shape[0], _dptr(g.view(np.float64)), int(rhs)), ctx)
+    return g
+
+
+def celes_num_spheres(ctx):
+    return int(load().celes_num_spheres(ctx))
+
+
+def celes_nmax(ctx):
+    return int(load().celes_nmax(ctx))
+
+
+def celes_num_rhs(ctx):
+    return int(load().celes_num_rhs(ctx))
+
+
+def celes_coupling_terms(lmax):
+    """(idx (T, 5) int32 = (source row, receiving row, p, mu, kind), val (T,)) of the built-in table."""
+    lib = load()
+    n = lib.celes_coupling_terms(int(lmax), None, None, 0)
+    if n < 0:
+        raise CelesError(n, "celes_coupling_terms")
+    idx = np.zeros((n, 5), dtype=np.int32)
+    val = np.zeros(n, dtype=np.float64)
+    lib.celes_coupling_terms(int(lmax), idx.ctypes.data_as(_ip), _dptr(val), n)
+    return idx, val
+
+
+def celes_profile(ctx, on):
+    return _check(load().celes_profile(ctx, int(bool(on))), ctx)
+
+
+KERNEL_FP32_COUPLING = 0
+KERNEL_FP64_COUPLING = 1
+KERNEL_EPILOGUE = 2
+
+
+def celes_kernel_time(ctx, which):
+    """(total milliseconds, launches) recorded since celes_profile(ctx, 1)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().celes_kernel_time(ctx, int(which), ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def celes_kernel_launches():
+    return int(load().celes_kernel_launches())
+
+
+def celes_destroy(ctx):
+    if ctx:
+        load().celes_destroy(ctx)
+
+
+def celes_last_error(ctx):
+    m = load().celes_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def celes_version():
+    return load().celes_version().decode()

@@ -1,0 +1,1000 @@
+// C ABI and host runtime of the solver: context and device memory, incident
+// fields, coupling / master matvecs, block preconditioner, GMRES in FP64 and
+// FP32 with FP64 iterative refinement (Sec. 3.2), far field (App. D).
+//
+// All arithmetic on problem data runs in the CUDA kernels of this library;
+// the host side holds only bookkeeping, the Givens rotations of the small
+// GMRES Hessenberg matrix and the cuboid partition of the preconditioner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/celes.h"
+#include "coupling_kernel.cuh"
+#include "kernels.h"
+
+namespace celes {
+// per-degree coupling launchers (coupling_L*.cu)
+#define CELES_DECLARE(LL)                                                                                   \
+  cudaError_t launch_coupling_partial_##LL(int precision, int64_t N, const void* pos, const void* x,       \
+                                            void* partial, double k, int chunks, cudaStream_t st);         \
+  int coupling_rpb_##LL(int precision);                                                                    \
+  int coupling_terms_export_##LL(int* idx, double* val, int cap);
+CELES_DECLARE(1)
+CELES_DECLARE(2)
+CELES_DECLARE(3)
+CELES_DECLARE(4)
+CELES_DECLARE(5)
+#undef CELES_DECLARE
+
+cudaError_t launch_coupling_partial(int L, int precision, int64_t N, const void* pos, const void* x, void* partial,
+                                    double k, int chunks, cudaStream_t st) {
+  switch (L) {
+    case 1: return launch_coupling_partial_1(precision, N, pos, x, partial, k, chunks, st);
+    case 2: return launch_coupling_partial_2(precision, N, pos, x, partial, k, chunks, st);
+    case 3: return launch_coupling_partial_3(precision, N, pos, x, partial, k, chunks, st);
+    case 4: return launch_coupling_partial_4(precision, N, pos, x, partial, k, chunks, st);
+    case 5: return launch_coupling_partial_5(precision, N, pos, x, partial, k, chunks, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+int coupling_receivers_per_block(int L, int precision) {
+  switch (L) {
+    case 1: return coupling_rpb_1(precision);
+    case 2: return coupling_rpb_2(precision);
+    case 3: return coupling_rpb_3(precision);
+    case 4: return coupling_rpb_4(precision);
+    case 5: return coupling_rpb_5(precision);
+    default: return 0;
+  }
+}
+int coupling_terms_export(int L, int* idx, double* val, int cap) {
+  switch (L) {
+    case 1: return coupling_terms_export_1(idx, val, cap);
+    case 2: return coupling_terms_export_2(idx, val, cap);
+    case 3: return coupling_terms_export_3(idx, val, cap);
+    case 4: return coupling_terms_export_4(idx, val, cap);
+    case 5: return coupling_terms_export_5(idx, val, cap);
+    default: return -1;
+  }
+}
+}  // namespace celes
+
+using namespace celes;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    if (b == 0) return cudaSuccess;
+    const cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    else p = nullptr;
+    return e;
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct celes_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t N = 0;
+  int L = 0, NH = 0, nmax = 0;
+  double n0 = 1.0, k0 = 0.0, k = 0.0;
+  int chunks_opt = 0;
+  DevBuf pos, radii, nrel, tq, tq32, tdiag;
+  int nrhs = 0;
+  DevBuf ain, rhs, b, x0;
+  bool has_b = false, has_x0 = false;
+  DevBuf partial;
+  // preconditioner
+  bool has_precond = false;
+  int64_t nblocks = 0;
+  int max_block_dim = 0;
+  DevBuf block_off, mat_off, perm, mats, piv, info, pwork;
+  // small device scratch
+  DevBuf dots, dot_partial, flag;
+  std::string err;
+  // kernel timing (celes_profile)
+  bool profiling = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int which;
+  };
+  std::vector<Rec> recs;
+  double prof_ms[3] = {0, 0, 0};
+  int64_t prof_n[3] = {0, 0, 0};
+};
+
+static std::atomic<int64_t> g_launches{0};
+
+namespace {
+
+int fail(celes_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(celes_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, CELES_ENOMEM, "%s: device allocation failed", what);
+  }
+  return fail(c, CELES_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ck_status(celes_ctx* c, cudaError_t e, const char* what) { return e == cudaSuccess ? CELES_OK : cuda_fail(c, e, what); }
+
+// CK(expression returning cudaError_t, "what"): return a celes_status on error
+#define CK(...)                                   \
+  do {                                            \
+    const int rc_ = ck_status(c, __VA_ARGS__);    \
+    if (rc_ != CELES_OK) return rc_;              \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaStream_t pick_stream(celes_ctx* c, void* s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+int auto_chunks(const celes_ctx* c, int precision) {
+  if (c->chunks_opt > 0) return c->chunks_opt;
+  const int rpb = coupling_receivers_per_block(c->L, precision);
+  const int64_t rb = (c->N + rpb - 1) / rpb;
+  const int64_t target = 152 * 2 * 4;  // about four waves of two CTAs per SM
+  int64_t ch = (target + rb - 1) / rb;
+  const int64_t max_by_src = std::max<int64_t>(1, c->N / 64);
+  ch = std::min<int64_t>(ch, max_by_src);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ch, 256)));
+}
+
+// coupling (mode 0: y = W x) or master (mode 1: y = x - T W x) products
+int prof_begin(celes_ctx* c, cudaStream_t st, celes_ctx::Rec& r, int which) {
+  r.which = which;
+  CK(cudaEventCreate(&r.a), "event");
+  CK(cudaEventCreate(&r.b), "event");
+  CK(cudaEventRecord(r.a, st), "event");
+  return CELES_OK;
+}
+
+int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision, int mode, cudaStream_t st) {
+  const int chunks = auto_chunks(c, precision);
+  const size_t elem = precision == CELES_FP64 ? 16 : 8;
+  const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
+  CK(c->partial.ensure(per * chunks), "coupling scratch");
+  for (int r = 0; r < nrhs; ++r) {
+    const char* xr = static_cast<const char*>(x) + per * r;
+    char* yr = static_cast<char*>(y) + per * r;
+    celes_ctx::Rec rec{};
+    if (c->profiling) {
+      int s = prof_begin(c, st, rec, precision == CELES_FP64 ? 1 : 0);
+      if (s) return s;
+    }
+    CK(launch_coupling_partial(c->L, precision, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st), "coupling kernel");
+    if (c->profiling) {
+      CK(cudaEventRecord(rec.b, st), "event");
+      c->recs.push_back(rec);
+      int s = prof_begin(c, st, rec, 2);
+      if (s) return s;
+    }
+    if (precision == CELES_FP64)
+      CK(launch_coupling_epilogue<double>(c->N, c->L, chunks, c->partial.p, xr, c->tq.p, yr, mode, st), "epilogue");
+    else
+      CK(launch_coupling_epilogue<float>(c->N, c->L, chunks, c->partial.p, xr, c->tq32.p, yr, mode, st), "epilogue");
+    if (c->profiling) {
+      CK(cudaEventRecord(rec.b, st), "event");
+      c->recs.push_back(rec);
+    }
+    g_launches += 2;
+  }
+  return CELES_OK;
+}
+
+void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
+  // Newton's iteration on P_n from the Chebyshev-like first guess
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = n == 1 ? z : p1;
+      const double pm = n == 1 ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      const double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (b - a) * (z + 1.0) + a;
+    w[i] = (b - a) / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// creation / destruction
+// ---------------------------------------------------------------------------
+extern "C" int celes_create(celes_ctx** out, int64_t N, const double* positions, const double* radii,
+                            const double* n_i, double n0, double k0, int lmax, const celes_options* opt) {
+  if (!out) return CELES_EINVAL;
+  *out = nullptr;
+  if (N < 1 || !positions || !radii || !n_i || lmax < 1 || lmax > 5 || !(n0 > 0.0) || !(k0 > 0.0) ||
+      N > (int64_t)1 << 30)
+    return CELES_EINVAL;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!(radii[i] > 0.0) || !std::isfinite(positions[3 * i]) || !std::isfinite(positions[3 * i + 1]) ||
+        !std::isfinite(positions[3 * i + 2]))
+      return CELES_EINVAL;
+  }
+  std::unique_ptr<celes_ctx> c(new celes_ctx());
+  c->device = opt ? opt->device : 0;
+  c->chunks_opt = opt ? opt->chunks : 0;
+  const int check_overlap = opt ? opt->check_overlap : 1;
+  c->N = N;
+  c->L = lmax;
+  c->NH = lmax * (lmax + 2);
+  c->nmax = 2 * c->NH;
+  c->n0 = n0;
+  c->k0 = k0;
+  c->k = n0 * k0;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return CELES_ECUDA;
+  }
+  if (c->device < 0 || c->device >= ndev) return CELES_EINVAL;
+  DeviceGuard dg(c->device);
+  celes_ctx* cp = c.get();
+#define CKC(expr, what)                                   \
+  do {                                                    \
+    const cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) {                              \
+      cudaGetLastError();                                 \
+      return e_ == cudaErrorMemoryAllocation ? CELES_ENOMEM : CELES_ECUDA; \
+    }                                                     \
+  } while (0)
+  CKC(cudaStreamCreateWithFlags(&cp->stream, cudaStreamNonBlocking), "stream");
+  std::vector<Pos4> hp(N);
+  for (int64_t i = 0; i < N; ++i) hp[i] = Pos4{positions[3 * i], positions[3 * i + 1], positions[3 * i + 2], 0.0};
+  std::vector<double> hn(2 * N);
+  for (int64_t i = 0; i < N; ++i) {
+    hn[2 * i] = n_i[2 * i] / n0;
+    hn[2 * i + 1] = n_i[2 * i + 1] / n0;
+  }
+  CKC(cp->pos.ensure(sizeof(Pos4) * N), "positions");
+  CKC(cp->radii.ensure(sizeof(double) * N), "radii");
+  CKC(cp->nrel.ensure(sizeof(double) * 2 * N), "n");
+  CKC(cp->tq.ensure(sizeof(double) * 2 * N * 2 * lmax), "tq");
+  CKC(cp->tq32.ensure(sizeof(float) * 2 * N * 2 * lmax), "tq32");
+  CKC(cp->tdiag.ensure(sizeof(double) * 2 * N * cp->nmax), "tdiag");
+  CKC(cp->flag.ensure(sizeof(int) * 4), "flag");
+  CKC(cudaMemcpyAsync(cp->pos.p, hp.data(), sizeof(Pos4) * N, cudaMemcpyHostToDevice, cp->stream), "h2d");
+  CKC(cudaMemcpyAsync(cp->radii.p, radii, sizeof(double) * N, cudaMemcpyHostToDevice, cp->stream), "h2d");
+  CKC(cudaMemcpyAsync(cp->nrel.p, hn.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice, cp->stream), "h2d");
+  if (check_overlap) {
+    CKC(cudaMemsetAsync(cp->flag.p, 0, sizeof(int), cp->stream), "memset");
+    CKC(launch_overlap_check(N, cp->pos.p, cp->radii.as<double>(), cp->flag.as<int>(), cp->stream), "overlap");
+    int h = 0;
+    CKC(cudaMemcpyAsync(&h, cp->flag.p, sizeof(int), cudaMemcpyDeviceToHost, cp->stream), "d2h");
+    CKC(cudaStreamSynchronize(cp->stream), "sync");
+    if (h) {
+      cudaStreamDestroy(cp->stream);
+      cp->stream = nullptr;
+      return CELES_EOVERLAP;
+    }
+  }
+  CKC(launch_mie(N, lmax, cp->k, cp->radii.as<double>(), cp->nrel.as<double>(), cp->tq.as<double>(), cp->stream),
+      "mie");
+  CKC(launch_tq_expand(N, lmax, cp->tq.as<double>(), cp->tdiag.as<double>(), cp->tq32.as<float>(), cp->stream),
+      "tq expand");
+  CKC(cudaMemsetAsync(cp->flag.p, 0, sizeof(int), cp->stream), "memset");
+  CKC(launch_nonfinite<double>(4 * N * lmax, cp->tq.p, cp->flag.as<int>(), cp->stream), "scan");
+  int bad = 0;
+  CKC(cudaMemcpyAsync(&bad, cp->flag.p, sizeof(int), cudaMemcpyDeviceToHost, cp->stream), "d2h");
+  CKC(cudaStreamSynchronize(cp->stream), "sync");
+#undef CKC
+  if (bad) {
+    cudaStreamDestroy(cp->stream);
+    cp->stream = nullptr;
+    return CELES_ENUMERIC;
+  }
+  *out = c.release();
+  return CELES_OK;
+}
+
+static void prof_flush(celes_ctx* c);
+
+extern "C" void celes_destroy(celes_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard dg(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    prof_flush(c);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    c->pos.release();
+    c->radii.release();
+    c->nrel.release();
+    c->tq.release();
+    c->tq32.release();
+    c->tdiag.release();
+    c->ain.release();
+    c->rhs.release();
+    c->b.release();
+    c->x0.release();
+    c->partial.release();
+    c->block_off.release();
+    c->mat_off.release();
+    c->perm.release();
+    c->mats.release();
+    c->piv.release();
+    c->info.release();
+    c->pwork.release();
+    c->dots.release();
+    c->dot_partial.release();
+    c->flag.release();
+  }
+  delete c;
+}
+
+static void prof_flush(celes_ctx* c) {
+  for (auto& r : c->recs) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.which] += ms;
+      c->prof_n[r.which] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->recs.clear();
+  cudaGetLastError();
+}
+
+extern "C" int celes_profile(celes_ctx* c, int on) {
+  if (!c) return CELES_EINVAL;
+  DeviceGuard dg(c->device);
+  prof_flush(c);
+  if (on) {
+    for (int q = 0; q < 3; ++q) {
+      c->prof_ms[q] = 0.0;
+      c->prof_n[q] = 0;
+    }
+  }
+  c->profiling = on != 0;
+  return CELES_OK;
+}
+
+extern "C" int celes_kernel_time(celes_ctx* c, int which, double* ms, int64_t* launches) {
+  if (!c) return CELES_EINVAL;
+  if (which < 0 || which > 2 || !ms || !launches) return fail(c, CELES_EINVAL, "kernel_time: bad arguments");
+  DeviceGuard dg(c->device);
+  prof_flush(c);
+  *ms = c->prof_ms[which];
+  *launches = c->prof_n[which];
+  return CELES_OK;
+}
+
+extern "C" int64_t celes_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" const char* celes_last_error(const celes_ctx* c) { return c ? c->err.c_str() : "null context"; }
+extern "C" const char* celes_version(void) { return "celes-gb300 0.1 (sm_103a)"; }
+extern "C" int64_t celes_num_spheres(const celes_ctx* c) { return c ? c->N : 0; }
+extern "C" int celes_nmax(const celes_ctx* c) { return c ? c->nmax : 0; }
+extern "C" int celes_num_rhs(const celes_ctx* c) { return c ? c->nrhs : 0; }
+
+extern "C" int celes_coupling_terms(int lmax, int* idx, double* val, int cap) {
+  if (lmax < 1 || lmax > 5 || cap < 0) return CELES_EINVAL;
+  return coupling_terms_export(lmax, idx, val, cap);
+}
+
+// ---------------------------------------------------------------------------
+// incident field
+// ---------------------------------------------------------------------------
+extern "C" int celes_set_incident(celes_ctx* c, const celes_incident* inc, int nrhs) {
+  if (!c) return CELES_EINVAL;
+  if (!inc || nrhs < 1) return fail(c, CELES_EINVAL, "set_incident: need nrhs >= 1 descriptors");
+  for (int r = 0; r < nrhs; ++r) {
+    const celes_incident& d = inc[r];
+    if (d.kind != CELES_PLANE_WAVE && d.kind != CELES_GAUSSIAN_BEAM)
+      return fail(c, CELES_EINVAL, "set_incident: unknown kind %d", d.kind);
+    if (d.kind == CELES_PLANE_WAVE && d.pol != 1 && d.pol != 2)
+      return fail(c, CELES_EINVAL, "set_incident: pol must be 1 or 2");
+    if (d.kind == CELES_GAUSSIAN_BEAM && !(d.waist > 0.0))
+      return fail(c, CELES_EINVAL, "set_incident: waist must be > 0");
+    if (d.kind == CELES_GAUSSIAN_BEAM && (d.n_beta < 0 || d.n_beta > 100000))
+      return fail(c, CELES_EINVAL, "set_incident: n_beta out of range");
+  }
+  DeviceGuard dg(c->device);
+  const size_t per = sizeof(double) * 2 * c->N * c->nmax;
+  CK(c->ain.ensure(per * nrhs), "a_in");
+  CK(c->rhs.ensure(per * nrhs), "rhs");
+  CK(c->b.ensure(per * nrhs), "b");
+  c->nrhs = nrhs;
+  c->has_b = false;
+  c->has_x0 = false;
+  DevBuf nodes, weights;
+  for (int r = 0; r < nrhs; ++r) {
+    const celes_incident& d = inc[r];
+    double* a = reinterpret_cast<double*>(c->ain.as<char>() + per * r);
+    if (d.kind == CELES_PLANE_WAVE) {
+      CK(launch_plane_wave(c->N, c->L, c->k, c->pos.p, d.beta, d.alpha, d.pol, d.E0_re, d.E0_im, a, c->stream),
+         "plane wave");
+    } else {
+      const int nb = d.n_beta > 0 ? d.n_beta : 128;
+      // beta range: the Gaussian factor exp(-w^2 k^2 sin^2(beta)/4) is below
+      // 1e-17 beyond sin^2(beta) = 39.2 / (w k / 2)^2
+      const double aa = std::pow(d.waist * c->k, 2) / 4.0;
+      const double s2 = 39.2 / aa;
+      const double bmax = s2 >= 1.0 ? M_PI / 2 : std::asin(std::sqrt(s2));
+      std::vector<double> hx, hw;
+      gauss_legendre(nb, 0.0, bmax, hx, hw);
+      CK(nodes.ensure(sizeof(double) * nb), "nodes");
+      CK(weights.ensure(sizeof(double) * nb), "weights");
+      CK(cudaMemcpyAsync(nodes.p, hx.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->stream), "h2d");
+      CK(cudaMemcpyAsync(weights.p, hw.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->stream), "h2d");
+      CK(launch_gaussian_beam(c->N, c->L, c->k, c->pos.p, d.waist, d.focus, d.alpha_G, d.E0_re, d.E0_im, nb,
+                              nodes.as<double>(), weights.as<double>(), a, c->stream),
+         "gaussian beam");
+      CK(cudaStreamSynchronize(c->stream), "sync");  // nodes/weights are freed at scope end
+    }
+  }
+  CK(launch_tdiag_mul(c->N * c->nmax, nrhs, c->tdiag.as<double>(), c->ain.as<double>(), c->rhs.as<double>(),
+                      c->stream),
+     "T a");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return CELES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// matvecs and preconditioner apply (device pointers, stream ordered)
+// ---------------------------------------------------------------------------
+extern "C" int celes_coupling_matvec(celes_ctx* c, const void* x, void* y, int nrhs, int precision, void* stream) {
+  if (!c) return CELES_EINVAL;
+  if (!x || !y || nrhs < 1 || (precision != CELES_FP64 && precision != CELES_FP32))
+    return fail(c, CELES_EINVAL, "coupling_matvec: bad arguments");
+  if (x == y) return fail(c, CELES_EINVAL, "coupling_matvec: x and y must not overlap");
+  DeviceGuard dg(c->device);
+  return coupling_apply(c, x, y, nrhs, precision, 0, pick_stream(c, stream));
+}
+
+extern "C" int celes_master_matvec(celes_ctx* c, const void* x, void* y, int nrhs, int precision, void* stream) {
+  if (!c) return CELES_EINVAL;
+  if (!x || !y || nrhs < 1 || (precision != CELES_FP64 && precision != CELES_FP32))
+    return fail(c, CELES_EINVAL, "master_matvec: bad arguments");
+  if (x == y) return fail(c, CELES_EINVAL, "master_matvec: x and y must not overlap");
+  DeviceGuard dg(c->device);
+  return coupling_apply(c, x, y, nrhs, precision, 1, pick_stream(c, stream));
+}
+
+extern "C" int celes_precond_build(celes_ctx* c, double edge) {
+  if (!c) return CELES_EINVAL;
+  if (!(edge > 0.0)) return fail(c, CELES_EINVAL, "precond_build: edge must be > 0");
+  DeviceGuard dg(c->device);
+  // partition on the host (index bookkeeping only): cuboid of each centre,
+  // grid anchored at the minimum corner, order (z, y, x), stable inside
+  std::vector<Pos4> hp(c->N);
+  CK(cudaMemcpy(hp.data(), c->pos.p, sizeof(Pos4) * c->N, cudaMemcpyDeviceToHost), "d2h");
+  double lo[3] = {hp[0].x, hp[0].y, hp[0].z};
+  for (const Pos4& p : hp) {
+    lo[0] = std::min(lo[0], p.x);
+    lo[1] = std::min(lo[1], p.y);
+    lo[2] = std::min(lo[2], p.z);
+  }
+  std::vector<std::tuple<int64_t, int64_t, int64_t, int>> key(c->N);
+  for (int64_t i = 0; i < c->N; ++i) {
+    key[i] = std::make_tuple(static_cast<int64_t>(std::floor((hp[i].z - lo[2]) / edge)),
+                             static_cast<int64_t>(std::floor((hp[i].y - lo[1]) / edge)),
+                             static_cast<int64_t>(std::floor((hp[i].x - lo[0]) / edge)), static_cast<int>(i));
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int> perm(c->N);
+  std::vector<int64_t> boff{0};
+  for (int64_t q = 0; q < c->N; ++q) {
+    perm[q] = std::get<3>(key[q]);
+    if (q > 0 && (std::get<0>(key[q]) != std::get<0>(key[q - 1]) || std::get<1>(key[q]) != std::get<1>(key[q - 1]) ||
+                  std::get<2>(key[q]) != std::get<2>(key[q - 1])))
+      boff.push_back(q);
+  }
+  boff.push_back(c->N);
+  const int64_t nb = static_cast<int64_t>(boff.size()) - 1;
+  std::vector<int64_t> moff(nb + 1, 0);
+  int64_t max_pairs = 0, max_dim = 0;
+  for (int64_t q = 0; q < nb; ++q) {
+    const int64_t ns = boff[q + 1] - boff[q];
+    const int64_t n = ns * c->nmax;
+    moff[q + 1] = moff[q] + n * n;
+    max_pairs = std::max(max_pairs, ns * ns);
+    max_dim = std::max(max_dim, n);
+  }
+  c->has_precond = false;
+  CK(c->block_off.ensure(sizeof(int64_t) * (nb + 1)), "block offsets");
+  CK(c->mat_off.ensure(sizeof(int64_t) * (nb + 1)), "matrix offsets");
+  CK(c->perm.ensure(sizeof(int) * c->N), "perm");
+  CK(c->mats.ensure(sizeof(double) * 2 * moff[nb]), "LU factors");
+  CK(c->piv.ensure(sizeof(int) * c->N * c->nmax), "pivots");
+  CK(c->info.ensure(sizeof(int) * nb), "info");
+  CK(cudaMemcpyAsync(c->block_off.p, boff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, c->stream), "h2d");
+  CK(cudaMemcpyAsync(c->mat_off.p, moff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, c->stream), "h2d");
+  CK(cudaMemcpyAsync(c->perm.p, perm.data(), sizeof(int) * c->N, cudaMemcpyHostToDevice, c->stream), "h2d");
+  CK(launch_precond_assemble(c->L, nb, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->perm.as<int>(),
+                             c->pos.p, c->tq.as<double>(), c->k, c->mats.as<double>(), max_pairs, c->stream),
+     "precond assembly");
+  CK(launch_precond_lu(nb, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax, c->mats.as<double>(),
+                       c->piv.as<int>(), c->info.as<int>(), c->stream),
+     "precond LU");
+  std::vector<int> hinfo(nb);
+  CK(cudaMemcpyAsync(hinfo.data(), c->info.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream), "d2h");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  for (int64_t q = 0; q < nb; ++q)
+    if (hinfo[q] != 0) return fail(c, CELES_ENUMERIC, "precond_build: block %lld is singular", (long long)q);
+  c->nblocks = nb;
+  c->max_block_dim = static_cast<int>(max_dim);
+  c->has_precond = true;
+  return CELES_OK;
+}
+
+static int precond_apply_internal(celes_ctx* c, const void* x, void* y, int nrhs, int precision, cudaStream_t st) {
+  CK(c->pwork.ensure(sizeof(double) * 2 * c->N * c->nmax * nrhs), "precond work");
+  if (precision == CELES_FP64)
+    CK(launch_precond_apply<double>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
+                                    c->perm.as<int>(), c->mats.as<double>(), c->piv.as<int>(), c->N, nrhs, x, y,
+                                    c->pwork.as<double>(), c->max_block_dim, st),
+       "precond apply");
+  else
+    CK(launch_precond_apply<float>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
+                                   c->perm.as<int>(), c->mats.as<double>(), c->piv.as<int>(), c->N, nrhs, x, y,
+                                   c->pwork.as<double>(), c->max_block_dim, st),
+       "precond apply");
+  return CELES_OK;
+}
+
+extern "C" int celes_precond_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision, void* stream) {
+  if (!c) return CELES_EINVAL;
+  if (!x || !y || nrhs < 1 || (precision != CELES_FP64 && precision != CELES_FP32))
+    return fail(c, CELES_EINVAL, "precond_apply: bad arguments");
+  if (!c->has_precond) return fail(c, CELES_ESTATE, "precond_apply: no preconditioner built");
+  DeviceGuard dg(c->device);
+  return precond_apply_internal(c, x, y, nrhs, precision, pick_stream(c, stream));
+}
+
+// ---------------------------------------------------------------------------
+// GMRES (right preconditioned, restarted, classical Gram-Schmidt applied
+// twice, Givens rotations on the host)
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename R>
+struct Gmres {
+  celes_ctx* c;
+  int64_t n;        // unknowns of one RHS
+  int m;            // restart
+  bool precond;
+  DevBuf V, w, z;   // basis (m+1 vectors), work vectors
+  std::vector<std::complex<double>> H, cs_s, g;
+  std::vector<double> cs_c;
+  int prec() const { return sizeof(R) == 8 ? CELES_FP64 : CELES_FP32; }
+  size_t vbytes() const { return sizeof(R) * 2 * n; }
+  char* Vp(int j) { return V.as<char>() + vbytes() * j; }
+
+  int init() {
+    CK(V.ensure(vbytes() * (m + 1)), "Krylov basis");
+    CK(w.ensure(vbytes()), "work");
+    CK(z.ensure(vbytes()), "work");
+    CK(c->dots.ensure(sizeof(double) * 2 * (m + 2)), "dots");
+    CK(c->dot_partial.ensure(sizeof(double) * 2 * (m + 2) * vec_dot_blocks(n)), "dot partials");
+    return CELES_OK;
+  }
+  // h[0..nv) = V[0..nv)^H v, on the host
+  int dots(const void* Vbase, int nv, const void* v, std::vector<std::complex<double>>& h) {
+    CK(launch_multi_dotc<R>(n, nv, Vbase, n, v, c->dot_partial.as<double>(), c->dots.as<double>(), c->stream), "dot");
+    g_launches += 2;
+    h.resize(nv);
+    CK(cudaMemcpyAsync(h.data(), c->dots.p, sizeof(double) * 2 * nv, cudaMemcpyDeviceToHost, c->stream), "d2h");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return CELES_OK;
+  }
+  int norm(const void* v, double& out) {
+    std::vector<std::complex<double>> h;
+    int s = dots(v, 1, v, h);
+    if (s) return s;
+    out = std::sqrt(std::max(0.0, h[0].real()));
+    return CELES_OK;
+  }
+  // A v = M P^{-1} v
+  int apply_op(const void* v, void* out, int& nmv) {
+    const void* src = v;
+    if (precond) {
+      int s = precond_apply_internal(c, v, z.p, 1, prec(), c->stream);
+      if (s) return s;
+      src = z.p;
+    }
+    ++nmv;
+    return coupling_apply(c, src, out, 1, prec(), 1, c->stream);
+  }
+  // Solve A u = r with x = P^{-1} u accumulated into x (x += P^{-1} u).
+  // x0 of the Krylov iteration is zero.  r is not modified.  Stops when the
+  // residual estimate <= tol * ||r|| or after max_it iterations.
+  // hist_scale converts the estimate to the caller's relative residual.
+  int solve(const void* r, void* x, double tol, int max_it, int& its, double& rel_est, int& nmv,
+            std::vector<double>* hist, double hist_scale) {
+    double rnorm = 0.0;
+    int s = norm(r, rnorm);
+    if (s) return s;
+    its = 0;
+    rel_est = 1.0;
+    if (!(rnorm > 0.0)) {
+      rel_est = 0.0;
+      return CELES_OK;
+    }
+    if (!std::isfinite(rnorm)) return fail(c, CELES_ENUMERIC, "GMRES: non-finite residual");
+    // start: u = 0, residual r; restarts use the updated residual computed
+    // from the Arnoldi relation (no extra matvec), tracked by beta
+    CK(launch_axpby<R, R>(n, 1.0 / rnorm, r, 0.0, Vp(0), c->stream), "v0");
+    double beta = rnorm;  // current residual norm (estimate)
+    bool first = true;
+    while (its < max_it) {
+      if (!first) {
+        // explicit residual of the current correction: r - A u, where the
+        // correction so far is already folded into x; recompute from w
+        // (w holds r - A u_total, maintained below)
+        double nb = 0.0;
+        s = norm(w.p, nb);
+        if (s) return s;
+        beta = nb;
+        if (beta <= tol * rnorm) break;
+        CK(launch_axpby<R, R>(n, 1.0 / beta, w.p, 0.0, Vp(0), c->stream), "v0");
+      }
+      first = false;
+      H.assign((size_t)(m + 1) * m, 0.0);
+      cs_c.assign(m, 0.0);
+      cs_s.assign(m, 0.0);
+      g.assign(m + 1, 0.0);
+      g[0] = beta;
+      int kk = 0;
+      std::vector<std::complex<double>> h1, h2;
+      for (kk = 0; kk < m && its < max_it; ++kk) {
+        s = apply_op(Vp(kk), w.p, nmv);
+        if (s) return s;
+        // classical Gram-Schmidt, twice
+        s = dots(V.p, kk + 1, w.p, h1);
+        if (s) return s;
+        CK(cudaMemcpyAsync(c->dots.p, h1.data(), sizeof(double) * 2 * (kk + 1), cudaMemcpyHostToDevice, c->stream),
+           "h2d");
+        CK(launch_multi_axpy<R>(n, kk + 1, V.p, n, c->dots.as<double>(), 1.0, w.p, c->stream), "axpy");
+        s = dots(V.p, kk + 1, w.p, h2);
+        if (s) return s;
+        CK(cudaMemcpyAsync(c->dots.p, h2.data(), sizeof(double) * 2 * (kk + 1), cudaMemcpyHostToDevice, c->stream),
+           "h2d");
+        CK(launch_multi_axpy<R>(n, kk + 1, V.p, n, c->dots.as<double>(), 1.0, w.p, c->stream), "axpy");
+        for (int j = 0; j <= kk; ++j) H[(size_t)j * m + kk] = h1[j] + h2[j];
+        double hn = 0.0;
+        s = norm(w.p, hn);
+        if (s) return s;
+        if (!std::isfinite(hn)) return fail(c, CELES_ENUMERIC, "GMRES: non-finite Krylov vector");
+        H[(size_t)(kk + 1) * m + kk] = hn;
+        if (hn > 0.0) CK(launch_axpby<R, R>(n, 1.0 / hn, w.p, 0.0, Vp(kk + 1), c->stream), "normalise");
+        for (int j = 0; j < kk; ++j) {
+          const std::complex<double> a = H[(size_t)j * m + kk], b = H[(size_t)(j + 1) * m + kk];
+          H[(size_t)j * m + kk] = cs_c[j] * a + cs_s[j] * b;
+          H[(size_t)(j + 1) * m + kk] = -std::conj(cs_s[j]) * a + cs_c[j] * b;
+        }
+        const std::complex<double> a = H[(size_t)kk * m + kk], b = H[(size_t)(kk + 1) * m + kk];
+        if (std::abs(b) == 0.0) {
+          cs_c[kk] = 1.0;
+          cs_s[kk] = 0.0;
+        } else if (std::abs(a) == 0.0) {
+          cs_c[kk] = 0.0;
+          cs_s[kk] = 1.0;
+        } else {
+          const double den = std::sqrt(std::norm(a) + std::norm(b));
+          cs_c[kk] = std::abs(a) / den;
+          cs_s[kk] = (a / std::abs(a)) * std::conj(b) / den;
+        }
+        H[(size_t)kk * m + kk] = cs_c[kk] * a + cs_s[kk] * b;
+        H[(size_t)(kk + 1) * m + kk] = 0.0;
+        g[kk + 1] = -std::conj(cs_s[kk]) * g[kk];
+        g[kk] = cs_c[kk] * g[kk];
+        ++its;
+        rel_est = std::abs(g[kk + 1]) / rnorm;
+        if (hist) hist->push_back(rel_est * hist_scale);
+        if (std::abs(g[kk + 1]) <= tol * rnorm || hn == 0.0) {
+          ++kk;
+          break;
+        }
+      }
+      // y = H^{-1} g (upper triangular), u = V y, x += P^{-1} u
+      std::vector<std::complex<double>> y(kk);
+      for (int i = kk - 1; i >= 0; --i) {
+        std::complex<double> sacc = g[i];
+        for (int j = i + 1; j < kk; ++j) sacc -= H[(size_t)i * m + j] * y[j];
+        const std::complex<double> d = H[(size_t)i * m + i];
+        if (std::abs(d) == 0.0) return fail(c, CELES_ENUMERIC, "GMRES: singular Hessenberg");
+        y[i] = sacc / d;
+      }
+      CK(cudaMemcpyAsync(c->dots.p, y.data(), sizeof(double) * 2 * kk, cudaMemcpyHostToDevice, c->stream), "h2d");
+      CK(launch_multi_combine<R>(n, kk, V.p, n, c->dots.as<double>(), 0.0, z.p, c->stream), "combine");
+      if (precond) {
+        s = precond_apply_internal(c, z.p, z.p, 1, prec(), c->stream);
+        if (s) return s;
+      }
+      CK(launch_axpby<R, R>(n, 1.0, z.p, 1.0, x, c->stream), "update");
+      if (std::abs(g[kk]) <= tol * rnorm || its >= max_it) break;
+      // true residual of the correction for the restart: w = r - A x_corr is
+      // not available without the accumulated correction, so the caller's x
+      // must hold only this solve's correction (it does: solve() is called
+      // with x = 0 on entry); w = r - M x
+      s = coupling_apply(c, x, w.p, 1, prec(), 1, c->stream);
+      ++nmv;
+      if (s) return s;
+      CK(launch_axpby<R, R>(n, 1.0, r, -1.0, w.p, c->stream), "residual");
+    }
+    return CELES_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" int celes_set_initial_guess(celes_ctx* c, const double* b0) {
+  if (!c) return CELES_EINVAL;
+  if (!b0) return fail(c, CELES_EINVAL, "set_initial_guess: null pointer");
+  if (c->nrhs < 1) return fail(c, CELES_ESTATE, "set_initial_guess: call set_incident first");
+  DeviceGuard dg(c->device);
+  const size_t bytes = sizeof(double) * 2 * c->N * c->nmax * c->nrhs;
+  CK(c->x0.ensure(bytes), "x0");
+  CK(cudaMemcpy(c->x0.p, b0, bytes, cudaMemcpyHostToDevice), "h2d");
+  c->has_x0 = true;
+  return CELES_OK;
+}
+
+extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, celes_solve_info* info) {
+  if (!c) return CELES_EINVAL;
+  if (c->nrhs < 1) return fail(c, CELES_ESTATE, "solve: call set_incident first");
+  if (!(tol > 0.0)) return fail(c, CELES_EINVAL, "solve: tol must be > 0");
+  celes_solve_opts opt{CELES_SOLVE_MIXED, 100, 2000, 20, CELES_X0_TA, 1, 1e-5};
+  if (o) opt = *o;
+  if (opt.restart <= 0) opt.restart = 100;
+  if (opt.max_iter <= 0) opt.max_iter = 2000;
+  if (opt.max_outer <= 0) opt.max_outer = 20;
+  if (!(opt.inner_tol > 0.0)) opt.inner_tol = 1e-5;
+  if (opt.mode != CELES_SOLVE_FP64 && opt.mode != CELES_SOLVE_MIXED)
+    return fail(c, CELES_EINVAL, "solve: unknown mode %d", opt.mode);
+  if (opt.x0 == CELES_X0_USER && !c->has_x0) return fail(c, CELES_ESTATE, "solve: no user initial guess set");
+  DeviceGuard dg(c->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = c->N * c->nmax;
+  const size_t per64 = sizeof(double) * 2 * n;
+  const bool use_pc = opt.use_precond && c->has_precond;
+  std::vector<double> hist;
+  int total_its = 0, outer = 0, mv64 = 0, mv32 = 0;
+  double worst = 0.0;
+  int status = CELES_OK;
+  DevBuf r64, d64, r32, d32;
+  CK(r64.ensure(per64), "residual");
+  Gmres<double> g64{c, n, opt.restart, use_pc};
+  Gmres<float> g32{c, n, opt.restart, use_pc};
+  if (opt.mode == CELES_SOLVE_FP64) {
+    int s = g64.init();
+    if (s) return s;
+    CK(d64.ensure(per64), "correction");
+  } else {
+    int s = g32.init();
+    if (s) return s;
+    CK(r32.ensure(per64 / 2), "residual32");
+    CK(d32.ensure(per64 / 2), "correction32");
+  }
+  for (int rr = 0; rr < c->nrhs; ++rr) {
+    double* rhs = reinterpret_cast<double*>(c->rhs.as<char>() + per64 * rr);
+    double* b = reinterpret_cast<double*>(c->b.as<char>() + per64 * rr);
+    // initial guess
+    if (opt.x0 == CELES_X0_TA) CK(cudaMemcpyAsync(b, rhs, per64, cudaMemcpyDeviceToDevice, c->stream), "x0");
+    else if (opt.x0 == CELES_X0_USER)
+      CK(cudaMemcpyAsync(b, c->x0.as<char>() + per64 * rr, per64, cudaMemcpyDeviceToDevice, c->stream), "x0");
+    else CK(cudaMemsetAsync(b, 0, per64, c->stream), "x0");
+    double rhs_norm = 0.0;
+    {
+      int s = g64.norm(rhs, rhs_norm);
+      if (s) return s;
+    }
+    if (!(rhs_norm > 0.0)) {
+      CK(cudaMemsetAsync(b, 0, per64, c->stream), "zero");
+      continue;
+    }
+    double rel = 1.0;
+    if (opt.mode == CELES_SOLVE_FP64) {
+      int its_left = opt.max_iter - total_its;
+      while (true) {
+        // r = rhs - M b
+        int s = coupling_apply(c, b, r64.p, 1, CELES_FP64, 1, c->stream);
+        if (s) return s;
+        ++mv64;
+        CK(launch_axpby<double, double>(n, 1.0, rhs, -1.0, r64.p, c->stream), "residual");
+        double rn = 0.0;
+        s = g64.norm(r64.p, rn);
+        if (s) return s;
+        if (!std::isfinite(rn)) return fail(c, CELES_ENUMERIC, "solve: non-finite residual");
+        rel = rn / rhs_norm;
+        hist.push_back(rel);
+        if (rel <= tol || its_left <= 0) break;
+        int its = 0;
+        double est = 0.0;
+        CK(cudaMemsetAsync(d64.p, 0, per64, c->stream), "zero");
+        s = g64.solve(r64.p, d64.p, tol / rel, its_left, its, est, mv64, &hist, rel);
+        if (s) return s;
+        CK(launch_axpby<double, double>(n, 1.0, d64.p, 1.0, b, c->stream), "update");
+        total_its += its;
+        its_left -= its;
+        ++outer;
+        if (its == 0) break;
+      }
+    } else {
+      // FP32 inner solves with FP64 residuals (iterative refinement)
+      int its_left = opt.max_iter - total_its;
+      int k_outer = 0;
+      CK(launch_axpby<double, float>(n, 1.0, b, 0.0, d32.p, c->stream), "cast");
+      // first residual in FP32: r = rhs - M b
+      int s = coupling_apply(c, d32.p, r32.p, 1, CELES_FP32, 1, c->stream);
+      if (s) return s;
+      ++mv32;
+      CK(launch_axpby<double, float>(n, 1.0, rhs, -1.0, r32.p, c->stream), "residual32");
+      double rn = 0.0;
+      {
+        Gmres<float>& gg = g32;
+        s = gg.norm(r32.p, rn);
+        if (s) return s;
+      }
+      rel = rn / rhs_norm;
+      hist.push_back(rel);
+      while (true) {
+        if (k_outer > 0) {
+          s = coupling_apply(c, b, r64.p, 1, CELES_FP64, 1, c->stream);
+          if (s) return s;
+          ++mv64;
+          CK(launch_axpby<double, double>(n, 1.0, rhs, -1.0, r64.p, c->stream), "residual");
+          s = g64.norm(r64.p, rn);
+          if (s) return s;
+          if (!std::isfinite(rn)) return fail(c, CELES_ENUMERIC, "solve: non-finite residual");
+          rel = rn / rhs_norm;
+          hist.push_back(rel);
+          if (rel <= tol || its_left <= 0 || k_outer >= opt.max_outer) break;
+          CK(launch_axpby<double, float>(n, 1.0 / rn, r64.p, 0.0, r32.p, c->stream), "cast residual");
+        } else {
+          CK(launch_axpby<float, float>(n, 1.0 / rn, r32.p, 0.0, r32.p, c->stream), "scale");
+        }
+        const double inner_tol = std::max(opt.inner_tol, 0.3 * tol / rel);
+        CK(cudaMemsetAsync(d32.p, 0, per64 / 2, c->stream), "zero");
+        int its = 0;
+        double est = 0.0;
+        s = g32.solve(r32.p, d32.p, inner_tol, its_left, its, est, mv32, &hist, rel);
+        if (s) return s;
+        total_its += its;
+        its_left -= its;
+        // b += rn * d
+        CK(launch_axpby<float, double>(n, rn, d32.p, 1.0, b, c->stream), "update");
+        ++k_outer;
+        if (its == 0) break;
+      }
+      outer += k_outer;
+    }
+    worst = std::max(worst, rel);
+    if (rel > tol) status = CELES_ENOCONV;
+  }
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  c->has_b = true;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    info->status = status;
+    info->iterations = total_its;
+    info->outer = outer;
+    info->matvecs_fp64 = mv64;
+    info->matvecs_fp32 = mv32;
+    info->residual = worst;
+    info->seconds = secs;
+    info->history_len = 0;
+    if (info->history && info->history_cap > 0) {
+      const int nh = std::min<int>(info->history_cap, static_cast<int>(hist.size()));
+      std::memcpy(info->history, hist.data(), sizeof(double) * nh);
+      info->history_len = nh;
+    }
+  }
+  if (status == CELES_ENOCONV) return fail(c, CELES_ENOCONV, "solve: residual %.3e above tol %.3e", worst, tol);
+  return CELES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// results
+// ---------------------------------------------------------------------------
+extern "C" int celes_get_coefficients(celes_ctx* c, double* out) {
+  if (!c) return CELES_EINVAL;
+  if (!out) return fail(c, CELES_EINVAL, "get_coefficients: null pointer");
+  if (!c->has_b) return fail(c, CELES_ESTATE, "get_coefficients: no solution yet");
+  DeviceGuard dg(c->device);
+  CK(cudaMemcpy(out, c->b.p, sizeof(double) * 2 * c->N * c->nmax * c->nrhs, cudaMemcpyDeviceToHost), "d2h");
+  return CELES_OK;
+}
+
+extern "C" int celes_get_incident_coefficients(celes_ctx* c, double* out) {
+  if (!c) return CELES_EINVAL;
+  if (!out) return fail(c, CELES_EINVAL, "get_incident_coefficients: null pointer");
+  if (c->nrhs < 1) return fail(c, CELES_ESTATE, "get_incident_coefficients: call set_incident first");
+  DeviceGuard dg(c->device);
+  CK(cudaMemcpy(out, c->ain.p, sizeof(double) * 2 * c->N * c->nmax * c->nrhs, cudaMemcpyDeviceToHost), "d2h");
+  return CELES_OK;
+}
+
+extern "C" int celes_get_tmatrix(celes_ctx* c, double* out) {
+  if (!c) return CELES_EINVAL;
+  if (!out) return fail(c, CELES_EINVAL, "get_tmatrix: null pointer");
+  DeviceGuard dg(c->device);
+  CK(cudaMemcpy(out, c->tdiag.p, sizeof(double) * 2 * c->N * c->nmax, cudaMemcpyDeviceToHost), "d2h");
+  return CELES_OK;
+}
+
+extern "C" int celes_farfield(celes_ctx* c, const double* dirs, int64_t Nd, double* g, int rhs) {
+  if (!c) return CELES_EINVAL;
+  if (!dirs || !g || Nd < 1) return fail(c, CELES_EINVAL, "farfield: bad arguments");
+  if (!c->has_b) return fail(c, CELES_ESTATE, "farfield: no solution yet");
+  if (rhs < 0 || rhs >= c->nrhs) return fail(c, CELES_EINVAL, "farfield: rhs out of range");
+  DeviceGuard dg(c->device);
+  DevBuf dd, dg_;
+  CK(dd.ensure(sizeof(double) * 2 * Nd), "dirs");
+  CK(dg_.ensure(sizeof(double) * 4 * Nd), "g");
+  CK(cudaMemcpyAsync(dd.p, dirs, sizeof(double) * 2 * Nd, cudaMemcpyHostToDevice, c->stream), "h2d");
+  const double* b = reinterpret_cast<const double*>(c->b.as<char>() + sizeof(double) * 2 * c->N * c->nmax * rhs);
+  CK(launch_farfield(c->N, c->L, c->k, c->pos.p, b, Nd, dd.as<double>(), dg_.as<double>(), c->stream), "farfield");
+  CK(cudaMemcpyAsync(g, dg_.p, sizeof(double) * 4 * Nd, cudaMemcpyDeviceToHost, c->stream), "d2h");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return CELES_OK;
+}

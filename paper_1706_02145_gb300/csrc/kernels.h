@@ -1,0 +1,62 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace celes {
+
+// coupling: partial products per source chunk (coupling_L*.cu)
+cudaError_t launch_coupling_partial(int L, int precision, int64_t N, const void* pos, const void* x, void* partial,
+                                    double k, int chunks, cudaStream_t st);
+int coupling_receivers_per_block(int L, int precision);
+int coupling_term_count(int L);
+int coupling_terms_export(int L, int* idx, double* val, int cap);
+
+template <typename R>
+cudaError_t launch_coupling_epilogue(int64_t N, int L, int chunks, const void* partial, const void* x, const void* tq,
+                                     void* y, int mode, cudaStream_t st);
+
+cudaError_t launch_mie(int64_t N, int L, double k, const double* radii, const double* n_rel, double* tq,
+                       cudaStream_t st);
+cudaError_t launch_tq_expand(int64_t N, int L, const double* tq, double* tdiag, float* tq32, cudaStream_t st);
+cudaError_t launch_plane_wave(int64_t N, int L, double k, const void* pos, double beta, double alpha, int pol,
+                              double e0r, double e0i, double* a, cudaStream_t st);
+cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, double w, const double* focus,
+                                 double alphaG, double e0r, double e0i, int nb, const double* nodes,
+                                 const double* weights, double* a, cudaStream_t st);
+
+int vec_dot_blocks(int64_t n);
+template <typename R>
+cudaError_t launch_multi_dotc(int64_t n, int nv, const void* V, int64_t ldv, const void* w, double* partial,
+                              double* out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_multi_axpy(int64_t n, int nv, const void* V, int64_t ldv, const double* h, double alpha0, void* w,
+                              cudaStream_t st);
+template <typename R>
+cudaError_t launch_multi_combine(int64_t n, int nv, const void* V, int64_t ldv, const double* c, double beta, void* y,
+                                 cudaStream_t st);
+template <typename RX, typename RY>
+cudaError_t launch_axpby(int64_t n, double a, const void* x, double b, void* y, cudaStream_t st);
+cudaError_t launch_tdiag_mul(int64_t n_per_rhs, int nrhs, const double* tdiag, const double* x, double* y,
+                             cudaStream_t st);
+template <typename R>
+cudaError_t launch_nonfinite(int64_t n, const void* v, int* flag, cudaStream_t st);
+
+cudaError_t launch_farfield(int64_t N, int L, double k, const void* pos, const double* b, int64_t Nd,
+                            const double* dirs, double* g, cudaStream_t st);
+cudaError_t launch_overlap_check(int64_t N, const void* pos, const double* radii, int* flag, cudaStream_t st);
+
+// block-diagonal preconditioner (precond.cu)
+cudaError_t launch_precond_assemble(int L, int64_t nblocks, const int64_t* block_off, const int64_t* mat_off,
+                                    const int* perm, const void* pos, const double* tq, double k, double* mats,
+                                    int64_t max_pairs, cudaStream_t st);
+cudaError_t launch_precond_lu(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
+                              double* mats, int* piv, int* info, cudaStream_t st);
+template <typename R>
+cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
+                                 const int* perm, const double* mats, const int* piv, int64_t N, int nrhs,
+                                 const void* x, void* y, double* work, int max_block_dim, cudaStream_t st);
+
+}  // namespace celes
