@@ -55,10 +55,17 @@ typedef enum {
 
 typedef enum { CELES_FP64 = 0, CELES_FP32 = 1 } celes_precision;
 
+typedef enum {
+  CELES_KERNEL_AUTO = 0,    /* rotation-translation-rotation for FP32, direct for FP64 */
+  CELES_KERNEL_DIRECT = 1,  /* per-entry evaluation of W^{ij} (App. A.2 formula as printed) */
+  CELES_KERNEL_RTR = 2      /* W = D^H W_z D (rotation, axial translation, rotation), both precisions */
+} celes_kernel;
+
 typedef struct {
   int device;           /* CUDA device ordinal (default 0) */
   int check_overlap;    /* reject overlapping spheres (default 1) */
   int chunks;           /* source chunks of the coupling kernel; 0 = automatic */
+  int kernel;           /* celes_kernel: coupling-kernel variant (default AUTO) */
 } celes_options;
 
 typedef enum { CELES_PLANE_WAVE = 0, CELES_GAUSSIAN_BEAM = 1 } celes_incident_kind;
@@ -197,6 +204,13 @@ int celes_kernel_time(celes_ctx* ctx, int which, double* ms, int64_t* launches);
 
 /* Number of kernels this library has launched in the process so far. */
 int64_t celes_kernel_launches(void);
+
+/* Algorithmic flops per ordered sphere pair and right-hand side of the
+ * coupling matvec for degree lmax and kernel variant (celes_kernel): the
+ * direct per-entry evaluation counts 4 (a5 + b5 terms) + 12 NH^2 + 2 NS + 4
+ * nmax^2; the rotation-translation-rotation variant counts its own rotations,
+ * Wigner-d sums, axial build/apply and phases.  Host-only; -1 on bad lmax. */
+double celes_flops_per_pair(int lmax, int kernel);
 
 void celes_destroy(celes_ctx* ctx);
 const char* celes_last_error(const celes_ctx* ctx);

@@ -38,8 +38,14 @@ CELES_X0_USER = 1
 CELES_X0_ZERO = 2
 
 
+CELES_KERNEL_AUTO = 0
+CELES_KERNEL_DIRECT = 1
+CELES_KERNEL_RTR = 2
+
+
 class celes_options(ctypes.Structure):
-    _fields_ = [("device", ctypes.c_int), ("check_overlap", ctypes.c_int), ("chunks", ctypes.c_int)]
+    _fields_ = [("device", ctypes.c_int), ("check_overlap", ctypes.c_int), ("chunks", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 class celes_incident(ctypes.Structure):
@@ -92,6 +98,7 @@ SIGNATURES = [
     ("celes_profile", ctypes.c_int, [_c_ctx_p, ctypes.c_int]),
     ("celes_kernel_time", ctypes.c_int, [_c_ctx_p, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]),
     ("celes_kernel_launches", ctypes.c_int64, []),
+    ("celes_flops_per_pair", ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
     ("celes_destroy", None, [_c_ctx_p]),
     ("celes_last_error", ctypes.c_char_p, [_c_ctx_p]),
     ("celes_version", ctypes.c_char_p, []),
@@ -155,11 +162,12 @@ def _stream(s):
 # one Python function per C entry point
 # ---------------------------------------------------------------------------
 
-def celes_create(positions, radii, n_i, n0, k0, lmax, device=0, check_overlap=True, chunks=0):
+def celes_create(positions, radii, n_i, n0, k0, lmax, device=0, check_overlap=True, chunks=0,
+                 kernel=CELES_KERNEL_AUTO):
     pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1, 3)
     rad = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
     ni = np.ascontiguousarray(np.asarray(n_i, dtype=np.complex128).reshape(-1)).view(np.float64)
-    opt = celes_options(int(device), int(bool(check_overlap)), int(chunks))
+    opt = celes_options(int(device), int(bool(check_overlap)), int(chunks), int(kernel))
     ctx = _c_ctx_p()
     code = load().celes_create(ctypes.byref(ctx), pos.shape[0], _dptr(pos), _dptr(rad), _dptr(ni),
                                float(n0), float(k0), int(lmax), ctypes.byref(opt))
@@ -302,6 +310,10 @@ def celes_kernel_time(ctx, which):
 
 def celes_kernel_launches():
     return int(load().celes_kernel_launches())
+
+
+def celes_flops_per_pair(lmax, kernel=CELES_KERNEL_AUTO):
+    return float(load().celes_flops_per_pair(int(lmax), int(kernel)))
 
 
 def celes_destroy(ctx):

@@ -31,6 +31,10 @@ namespace celes {
   cudaError_t launch_coupling_partial_##LL(int precision, int64_t N, const void* pos, const void* x,       \
                                             void* partial, double k, int chunks, cudaStream_t st);         \
   int coupling_rpb_##LL(int precision);                                                                    \
+  cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
+                                       void* partial, double k, int chunks, cudaStream_t st);              \
+  int coupling_rtr_rpb_##LL(int precision);                                                                \
+  long long coupling_rtr_flops_##LL();                                                                     \
   int coupling_terms_export_##LL(int* idx, double* val, int cap);
 CELES_DECLARE(1)
 CELES_DECLARE(2)
@@ -48,6 +52,37 @@ cudaError_t launch_coupling_partial(int L, int precision, int64_t N, const void*
     case 4: return launch_coupling_partial_4(precision, N, pos, x, partial, k, chunks, st);
     case 5: return launch_coupling_partial_5(precision, N, pos, x, partial, k, chunks, st);
     default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t launch_coupling_rtr(int L, int precision, int64_t N, const void* pos, const void* x, void* partial,
+                                double k, int chunks, cudaStream_t st) {
+  switch (L) {
+    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st);
+    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st);
+    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st);
+    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st);
+    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+int coupling_rtr_receivers_per_block(int L, int precision) {
+  switch (L) {
+    case 1: return coupling_rtr_rpb_1(precision);
+    case 2: return coupling_rtr_rpb_2(precision);
+    case 3: return coupling_rtr_rpb_3(precision);
+    case 4: return coupling_rtr_rpb_4(precision);
+    case 5: return coupling_rtr_rpb_5(precision);
+    default: return 0;
+  }
+}
+long long coupling_rtr_flops(int L) {
+  switch (L) {
+    case 1: return coupling_rtr_flops_1();
+    case 2: return coupling_rtr_flops_2();
+    case 3: return coupling_rtr_flops_3();
+    case 4: return coupling_rtr_flops_4();
+    case 5: return coupling_rtr_flops_5();
+    default: return -1;
   }
 }
 int coupling_receivers_per_block(int L, int precision) {
@@ -111,6 +146,7 @@ struct celes_ctx {
   int L = 0, NH = 0, nmax = 0;
   double n0 = 1.0, k0 = 0.0, k = 0.0;
   int chunks_opt = 0;
+  int kernel = CELES_KERNEL_AUTO;
   DevBuf pos, radii, nrel, tq, tq32, tdiag;
   int nrhs = 0;
   DevBuf ain, rhs, b, x0;
@@ -183,9 +219,15 @@ struct DeviceGuard {
 
 cudaStream_t pick_stream(celes_ctx* c, void* s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
 
+bool use_rtr(const celes_ctx* c, int precision) {
+  (void)precision;
+  return c->kernel != CELES_KERNEL_DIRECT;
+}
+
 int auto_chunks(const celes_ctx* c, int precision) {
   if (c->chunks_opt > 0) return c->chunks_opt;
-  const int rpb = coupling_receivers_per_block(c->L, precision);
+  const int rpb = use_rtr(c, precision) ? coupling_rtr_receivers_per_block(c->L, precision)
+                                        : coupling_receivers_per_block(c->L, precision);
   const int64_t rb = (c->N + rpb - 1) / rpb;
   const int64_t target = 152 * 2 * 4;  // about four waves of two CTAs per SM
   int64_t ch = (target + rb - 1) / rb;
@@ -216,7 +258,12 @@ int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision
       int s = prof_begin(c, st, rec, precision == CELES_FP64 ? 1 : 0);
       if (s) return s;
     }
-    CK(launch_coupling_partial(c->L, precision, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st), "coupling kernel");
+    if (use_rtr(c, precision))
+      CK(launch_coupling_rtr(c->L, precision, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st),
+         "coupling kernel");
+    else
+      CK(launch_coupling_partial(c->L, precision, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st),
+         "coupling kernel");
     if (c->profiling) {
       CK(cudaEventRecord(rec.b, st), "event");
       c->recs.push_back(rec);
@@ -231,7 +278,6 @@ int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision
       CK(cudaEventRecord(rec.b, st), "event");
       c->recs.push_back(rec);
     }
-    g_launches += 2;
   }
   return CELES_OK;
 }
@@ -282,6 +328,8 @@ extern "C" int celes_create(celes_ctx** out, int64_t N, const double* positions,
   std::unique_ptr<celes_ctx> c(new celes_ctx());
   c->device = opt ? opt->device : 0;
   c->chunks_opt = opt ? opt->chunks : 0;
+  c->kernel = opt ? opt->kernel : CELES_KERNEL_AUTO;
+  if (c->kernel < CELES_KERNEL_AUTO || c->kernel > CELES_KERNEL_RTR) return CELES_EINVAL;
   const int check_overlap = opt ? opt->check_overlap : 1;
   c->N = N;
   c->L = lmax;
@@ -427,7 +475,17 @@ extern "C" int celes_kernel_time(celes_ctx* c, int which, double* ms, int64_t* l
   return CELES_OK;
 }
 
-extern "C" int64_t celes_kernel_launches(void) { return g_launches.load(); }
+extern "C" int64_t celes_kernel_launches(void) { return g_launches.load() + celes::kernel_launch_count(); }
+
+extern "C" double celes_flops_per_pair(int lmax, int kernel) {
+  if (lmax < 1 || lmax > 5) return -1.0;
+  if (kernel == CELES_KERNEL_DIRECT) {
+    // per-entry evaluation: 4 (A + B terms) + 12 NH^2 + 2 NS (build) + 4 nmax^2 (apply)
+    const int NH = lmax * (lmax + 2), NS = (2 * lmax + 1) * (2 * lmax + 2) / 2;
+    return 4.0 * coupling_terms_export(lmax, nullptr, nullptr, 0) + 12.0 * NH * NH + 2.0 * NS + 4.0 * (2.0 * NH) * (2.0 * NH);
+  }
+  return static_cast<double>(coupling_rtr_flops(lmax));
+}
 
 extern "C" const char* celes_last_error(const celes_ctx* c) { return c ? c->err.c_str() : "null context"; }
 extern "C" const char* celes_version(void) { return "celes-gb300 0.1 (sm_103a)"; }
@@ -640,7 +698,7 @@ struct Gmres {
   // h[0..nv) = V[0..nv)^H v, on the host
   int dots(const void* Vbase, int nv, const void* v, std::vector<std::complex<double>>& h) {
     CK(launch_multi_dotc<R>(n, nv, Vbase, n, v, c->dot_partial.as<double>(), c->dots.as<double>(), c->stream), "dot");
-    g_launches += 2;
+
     h.resize(nv);
     CK(cudaMemcpyAsync(h.data(), c->dots.p, sizeof(double) * 2 * nv, cudaMemcpyDeviceToHost, c->stream), "d2h");
     CK(cudaStreamSynchronize(c->stream), "sync");

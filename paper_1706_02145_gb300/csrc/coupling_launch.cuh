@@ -8,6 +8,8 @@
 #include <cstdint>
 
 #include "coupling_kernel.cuh"
+#include "rtr_kernel.cuh"
+#include "kernels.h"
 
 namespace celes {
 
@@ -31,6 +33,7 @@ cudaError_t launch_coupling_partial_t(int64_t N, const void* pos, const void* x,
   coupling_partial_kernel<L, R><<<grid, C::BLOCK, smem, st>>>(
       static_cast<int>(N), static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
       static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk));
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -66,6 +69,42 @@ cudaError_t launch_generic_coupling_fp64(int L, int64_t N, const void* pos, cons
 constexpr int kGenericRPB = 64;
 
 // FP64_UNROLLED: 1 = compile-time FP64 kernel, 0 = runtime-table FP64 kernel
+// Algorithmic flops per ordered sphere pair and RHS of the rotation-
+// translation-rotation evaluation, counted from the same compile-time tables
+// the kernel uses (FMA = 2 flops, complex multiply = 6, complex MAC = 8):
+//   z-rotation of x+- (2 NH complex multiplies), Wigner-d entries (monomials
+//   and one FMA per term, evaluated twice), forward and backward block
+//   rotations (8 flops per R entry each), axial build (4 flops per term plus 4
+//   for the W+- combination per (mu >= 0, l, l') block), axial apply (2 complex
+//   MACs per (mu, l, l')), output phase (2 NH complex MACs), h_p recurrence.
+template <int L>
+long long rtr_flops_per_pair_t() {
+  long long f = 0;
+  constexpr int NH = L * (L + 2);
+  f += 2LL * NH * 6;                                   // e^{i m phi} x+-
+  f += 2LL * (4 * L - 2) + 8;                          // h_p recurrence and start
+  long long rot = 0, dm = 0;
+  auto per_l = [&](auto LL_) {
+    constexpr int l = decltype(LL_)::value;
+    rot += 8LL * (2 * l + 1) * (2 * l + 1);
+    dm += (2 * l + 1) + 2LL * rtr::DTab<l>::value.off[rtr::DTab<l>::value.ncanon];
+  };
+  [&]<int... I>(std::integer_sequence<int, I...>) { (per_l(std::integral_constant<int, I + 1>{}), ...); }
+  (std::make_integer_sequence<int, L>{});
+  f += 2 * rot + 2 * dm;
+  for (int mu = 0; mu <= L; ++mu) {
+    for (int lo = (mu > 1 ? mu : 1); lo <= L; ++lo) {
+      for (int li = (mu > 1 ? mu : 1); li <= L; ++li) {
+        const rtr::AxialRow<L> a = rtr::make_axial<L>(mu, lo, li);
+        f += 4LL * (a.na + a.nb) + 4;
+        f += (mu > 0 ? 2 : 1) * 16LL;
+      }
+    }
+  }
+  f += 2LL * NH * 8;                                   // output phase and accumulate
+  return f;
+}
+
 #define CELES_INSTANTIATE_COUPLING(LL, FP64_UNROLLED)                                                       \
   cudaError_t launch_coupling_partial_##LL(int precision, int64_t N, const void* pos, const void* x,       \
                                             void* partial, double k, int chunks, cudaStream_t st) {        \
@@ -77,10 +116,19 @@ constexpr int kGenericRPB = 64;
     }                                                                                                      \
     return launch_coupling_partial_t<LL, float>(N, pos, x, partial, k, chunks, st);                        \
   }                                                                                                        \
+  cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
+                                       void* partial, double k, int chunks, cudaStream_t st) {             \
+    return precision == 0 ? rtr::launch_partial<LL, double>(N, pos, x, partial, k, chunks, st)             \
+                          : rtr::launch_partial<LL, float>(N, pos, x, partial, k, chunks, st);             \
+  }                                                                                                        \
+  int coupling_rtr_rpb_##LL(int precision) {                                                               \
+    return precision == 0 ? rtr::Config<LL, double>::BLOCK : rtr::Config<LL, float>::BLOCK;               \
+  }                                                                                                        \
   int coupling_rpb_##LL(int precision) {                                                                   \
     if (precision == 0) return (FP64_UNROLLED) ? CouplingLayout<LL, double>::RPB : kGenericRPB;           \
     return CouplingLayout<LL, float>::RPB;                                                                 \
   }                                                                                                        \
+  long long coupling_rtr_flops_##LL() { return rtr_flops_per_pair_t<LL>(); }                                 \
   int coupling_terms_export_##LL(int* idx, double* val, int cap) {                                         \
     return coupling_terms_export_t<LL>(idx, val, cap);                                                     \
   }

@@ -210,6 +210,7 @@ cudaError_t launch_precond_assemble(int L, int64_t nblocks, const int64_t* block
   dim3 grid(static_cast<unsigned>((max_pairs + 127) / 128), static_cast<unsigned>(nblocks));
   generic_assemble_kernel<<<grid, 128, 0, st>>>(L, T, block_off, mat_off, perm, static_cast<const Pos4*>(pos), tq, k,
                                                 reinterpret_cast<double2*>(mats));
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -299,6 +300,7 @@ cudaError_t launch_generic_coupling_fp64(int L, int64_t N, const void* pos, cons
   generic_coupling_kernel<<<grid, kGBlock, 0, st>>>(L, T, static_cast<int>(N), static_cast<const Pos4*>(pos),
                                                     static_cast<const double2*>(x), static_cast<double2*>(partial), k,
                                                     static_cast<int>(chunk));
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@
 //  * far-field amplitude g_j (App. D)
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "cmath.cuh"
@@ -15,6 +16,10 @@
 #include "kernels.h"
 
 namespace celes {
+
+static std::atomic<int64_t> g_launch_count{0};
+void note_launch(int n) { g_launch_count += n; }
+int64_t kernel_launch_count() { return g_launch_count.load(); }
 
 static __device__ __forceinline__ int row_l_rt(int r) {
   int l = static_cast<int>(sqrt(static_cast<double>(r + 1)));
@@ -72,6 +77,7 @@ cudaError_t launch_coupling_epilogue(int64_t N, int L, int chunks, const void* p
   coupling_epilogue_kernel<R><<<grid > 0 ? grid : 1, threads, 0, st>>>(
       N, L, chunks, static_cast<const Pair2<R>*>(partial), static_cast<const Pair2<R>*>(x),
       static_cast<const Pair2<R>*>(tq), static_cast<Pair2<R>*>(y), mode);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_coupling_epilogue<float>(int64_t, int, int, const void*, const void*, const void*, void*,
@@ -119,6 +125,7 @@ cudaError_t launch_mie(int64_t N, int L, double k, const double* radii, const do
                        cudaStream_t st) {
   const int threads = 128;
   mie_kernel<<<static_cast<unsigned>((N + threads - 1) / threads), threads, 0, st>>>(N, L, k, radii, n_rel, tq);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -147,6 +154,7 @@ cudaError_t launch_tq_expand(int64_t N, int L, const double* tq, double* tdiag, 
   const int64_t total = N * (L * (L + 2) > 2 * L ? L * (L + 2) : 2 * L);
   const int threads = 256;
   tq_expand_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, st>>>(N, L, tq, tdiag, tq32);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -192,6 +200,7 @@ cudaError_t launch_plane_wave(int64_t N, int L, double k, const void* pos, doubl
   const int threads = 128;
   plane_wave_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, st>>>(
       N, L, k, static_cast<const Pos4*>(pos), beta, alpha, pol, e0r, e0i, a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -253,6 +262,7 @@ cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, do
   gaussian_beam_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, st>>>(
       N, L, k, static_cast<const Pos4*>(pos), w, focus[0], focus[1], focus[2], alphaG, e0r, e0i, nb, nodes, weights,
       a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -338,6 +348,7 @@ cudaError_t launch_multi_dotc(int64_t n, int nv, const void* V, int64_t ldv, con
   multi_dotc_kernel<R><<<nb, kVecThreads, 0, st>>>(n, nv, static_cast<const Pair2<R>*>(V), ldv,
                                                    static_cast<const Pair2<R>*>(w), partial);
   reduce_partials_kernel<<<nv, 256, 0, st>>>(nb, nv, partial, out);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_multi_dotc<float>(int64_t, int, const void*, int64_t, const void*, double*, double*,
@@ -391,6 +402,7 @@ cudaError_t launch_multi_axpy(int64_t n, int nv, const void* V, int64_t ldv, con
                               cudaStream_t st) {
   multi_axpy_kernel<R><<<vec_grid(n), kVecThreads, 0, st>>>(n, nv, static_cast<const Pair2<R>*>(V), ldv, h, alpha0,
                                                             static_cast<Pair2<R>*>(w));
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_multi_axpy<float>(int64_t, int, const void*, int64_t, const double*, double, void*,
@@ -403,6 +415,7 @@ cudaError_t launch_multi_combine(int64_t n, int nv, const void* V, int64_t ldv, 
                                  cudaStream_t st) {
   multi_combine_kernel<R><<<vec_grid(n), kVecThreads, 0, st>>>(n, nv, static_cast<const Pair2<R>*>(V), ldv, c, beta,
                                                                static_cast<Pair2<R>*>(y));
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_multi_combine<float>(int64_t, int, const void*, int64_t, const double*, double, void*,
@@ -427,6 +440,7 @@ template <typename RX, typename RY>
 cudaError_t launch_axpby(int64_t n, double a, const void* x, double b, void* y, cudaStream_t st) {
   axpby_kernel<RX, RY><<<vec_grid(n), kVecThreads, 0, st>>>(n, a, static_cast<const Pair2<RX>*>(x), b,
                                                             static_cast<Pair2<RY>*>(y));
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_axpby<float, float>(int64_t, double, const void*, double, void*, cudaStream_t);
@@ -449,6 +463,7 @@ __global__ void tdiag_mul_kernel(int64_t n_per_rhs, int nrhs, const double* __re
 cudaError_t launch_tdiag_mul(int64_t n_per_rhs, int nrhs, const double* tdiag, const double* x, double* y,
                              cudaStream_t st) {
   tdiag_mul_kernel<<<vec_grid(n_per_rhs * nrhs), kVecThreads, 0, st>>>(n_per_rhs, nrhs, tdiag, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -462,6 +477,7 @@ __global__ void nonfinite_kernel(int64_t n, const R* __restrict__ v, int* __rest
 template <typename R>
 cudaError_t launch_nonfinite(int64_t n, const void* v, int* flag, cudaStream_t st) {
   nonfinite_kernel<R><<<vec_grid(n), kVecThreads, 0, st>>>(n, static_cast<const R*>(v), flag);
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_nonfinite<float>(int64_t, const void*, int*, cudaStream_t);
@@ -532,6 +548,7 @@ cudaError_t launch_farfield(int64_t N, int L, double k, const void* pos, const d
     farfield_kernel<<<static_cast<unsigned>(nd), 256, smem, st>>>(N, L, k, static_cast<const Pos4*>(pos), b,
                                                                   dirs + 2 * d0, g + 4 * d0);
   }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -557,6 +574,7 @@ cudaError_t launch_overlap_check(int64_t N, const void* pos, const double* radii
   const int threads = 128;
   overlap_kernel<<<static_cast<unsigned>((N + threads - 1) / threads), threads, 0, st>>>(
       N, static_cast<const Pos4*>(pos), radii, flag);
+  note_launch();
   return cudaGetLastError();
 }
 

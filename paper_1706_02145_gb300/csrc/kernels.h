@@ -7,6 +7,10 @@
 
 namespace celes {
 
+// process-wide count of kernels launched by this library
+void note_launch(int n = 1);
+int64_t kernel_launch_count();
+
 // coupling: partial products per source chunk (coupling_L*.cu)
 cudaError_t launch_coupling_partial(int L, int precision, int64_t N, const void* pos, const void* x, void* partial,
                                     double k, int chunks, cudaStream_t st);

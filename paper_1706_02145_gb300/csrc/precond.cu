@@ -116,6 +116,7 @@ cudaError_t launch_precond_lu(int64_t nblocks, const int64_t* block_off, const i
   if (nblocks <= 0) return cudaSuccess;
   precond_lu_kernel<<<static_cast<unsigned>(nblocks), kLuThreads, 0, st>>>(
       block_off, mat_off, nmax, reinterpret_cast<double2*>(mats), piv, info);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -207,6 +208,7 @@ cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, cons
                                                 reinterpret_cast<const double2*>(mats), piv, N,
                                                 static_cast<const Pair2<R>*>(x), static_cast<Pair2<R>*>(y),
                                                 reinterpret_cast<double2*>(work));
+  note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_precond_apply<float>(int64_t, const int64_t*, const int64_t*, int, const int*,

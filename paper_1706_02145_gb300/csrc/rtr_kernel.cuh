@@ -1,0 +1,485 @@
+// Coupling matvec y_i = sum_{j != i} W^{ij} x_j by rotation-translation-
+// rotation (see rtr_tables.cuh for the factorisation W = D^H W_z D).
+//
+// Per ordered pair (i, j), one thread (the receiver's):
+//   1. geometry: k|d| (FP64 distance, FP64 phase reduction), h_p(k|d|),
+//      cos/sin(theta/2), e^{i m phi}
+//   2. x'+-[l, mu] = sum_m R^l_{mu m}(theta) e^{i m phi} x+-[l, m]
+//   3. y'+-[l, mu] = sum_{l'} (A_z +- i B_z)[l, l', mu] x'+-[l', mu]
+//      (built once for mu >= 0 and reused, B sign flipped, for -mu)
+//   4. y+-[l, m] += e^{-i m phi} sum_mu R^l_{mu m}(theta) y'+-[l, mu]
+// with x+- = x_1 +- x_2 (the tau structure [[A, B], [B, A]] of W, App. A.2).
+// All coefficients (Wigner-d sums, axial a5/b5 terms) are compile-time
+// immediates; one code stream serves every warp.  Per pair the thread does
+// O(L^3) work instead of the O(L^4) of the direct per-entry evaluation.
+#pragma once
+
+#include "coupling_kernel.cuh"
+#include "rtr_tables.cuh"
+#include "kernels.h"
+
+namespace celes {
+namespace rtr {
+
+template <int L, typename R>
+struct Geom {
+  R hre[2 * L + 1], him[2 * L + 1];
+  R cp[2 * L + 1], sp[2 * L + 1];  // powers of cos(theta/2), sin(theta/2)
+  R ere[L + 1], eim[L + 1];
+};
+
+template <int L, typename R>
+__device__ __forceinline__ void geometry(double dx, double dy, double dz, double k, Geom<L, R>& g) {
+  constexpr int PM = 2 * L;
+  const double d2 = fma_(dx, dx, fma_(dy, dy, dz * dz));
+  R ct, st, cph, sph;
+  if constexpr (sizeof(R) == 4) {
+    const float rinv = rsqrtf(static_cast<float>(d2));
+    double d = d2 * static_cast<double>(rinv);
+    d = fma_(0.5 * static_cast<double>(rinv), fma_(-d, d, d2), d);
+    const double kd = k * d;
+    float sn, cs;
+    sincos_kd(kd, sn, cs);
+    const float ix = 1.0f / static_cast<float>(kd);
+    g.hre[0] = sn * ix;
+    g.him[0] = -cs * ix;
+    g.hre[1] = -ix * fma_(-sn, ix, cs);
+    g.him[1] = -ix * fma_(cs, ix, sn);
+#pragma unroll
+    for (int p = 1; p < PM; ++p) {
+      const float a = static_cast<float>(2 * p + 1) * ix;
+      g.hre[p + 1] = fma_(a, g.hre[p], -g.hre[p - 1]);
+      g.him[p + 1] = fma_(a, g.him[p], -g.him[p - 1]);
+    }
+    const float id = static_cast<float>(1.0 / d);
+    const float dxf = static_cast<float>(dx), dyf = static_cast<float>(dy), dzf = static_cast<float>(dz);
+    const float rho = sqrtf(fma_(dxf, dxf, dyf * dyf));
+    ct = dzf * id;
+    st = rho * id;
+    const float ir = rho > 0.0f ? 1.0f / rho : 0.0f;
+    cph = rho > 0.0f ? dxf * ir : 1.0f;
+    sph = dyf * ir;
+  } else {
+    const double d = sqrt(d2);
+    const double kd = k * d;
+    const double TWO_PI = 6.283185307179586476925286766559;
+    const double ph = fma_(-rint(kd * (1.0 / TWO_PI)), TWO_PI, kd);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const double ix = 1.0 / kd;
+    g.hre[0] = sn * ix;
+    g.him[0] = -cs * ix;
+    g.hre[1] = -ix * fma_(-sn, ix, cs);
+    g.him[1] = -ix * fma_(cs, ix, sn);
+#pragma unroll
+    for (int p = 1; p < PM; ++p) {
+      const double a = static_cast<double>(2 * p + 1) * ix;
+      g.hre[p + 1] = fma_(a, g.hre[p], -g.hre[p - 1]);
+      g.him[p + 1] = fma_(a, g.him[p], -g.him[p - 1]);
+    }
+    const double id = 1.0 / d;
+    const double rho = sqrt(fma_(dx, dx, dy * dy));
+    ct = dz * id;
+    st = rho * id;
+    const double ir = rho > 0.0 ? 1.0 / rho : 0.0;
+    cph = rho > 0.0 ? dx * ir : 1.0;
+    sph = dy * ir;
+  }
+  // half angles without cancellation: c = sqrt((1+ct)/2), s = st/(2c) for
+  // ct >= 0, and the mirror formulas otherwise
+  R c, s;
+  if (ct >= static_cast<R>(0)) {
+    c = sqrt(static_cast<R>(0.5) * (static_cast<R>(1) + ct));
+    s = static_cast<R>(0.5) * st / c;
+  } else {
+    s = sqrt(static_cast<R>(0.5) * (static_cast<R>(1) - ct));
+    c = static_cast<R>(0.5) * st / s;
+  }
+  g.cp[0] = static_cast<R>(1);
+  g.sp[0] = static_cast<R>(1);
+#pragma unroll
+  for (int q = 1; q <= PM; ++q) {
+    g.cp[q] = g.cp[q - 1] * c;
+    g.sp[q] = g.sp[q - 1] * s;
+  }
+  g.ere[0] = static_cast<R>(1);
+  g.eim[0] = static_cast<R>(0);
+#pragma unroll
+  for (int m = 1; m <= L; ++m) {
+    g.ere[m] = fma_(g.ere[m - 1], cph, -g.eim[m - 1] * sph);
+    g.eim[m] = fma_(g.ere[m - 1], sph, g.eim[m - 1] * cph);
+  }
+}
+
+// ---- Wigner-d canonical entries of degree l --------------------------------
+template <int l, int T, typename R>
+__device__ __forceinline__ void dterm(const R* q, R& acc) {
+  constexpr R C = static_cast<R>(DTerm<l, T>::c);
+  acc = fma_(C, q[DTerm<l, T>::j], acc);
+}
+template <int l, int T0, typename R, int... K>
+__device__ __forceinline__ R dsum(const R* q, std::integer_sequence<int, K...>) {
+  R acc = static_cast<R>(0);
+  (dterm<l, T0 + K>(q, acc), ...);
+  return acc;
+}
+template <int l, typename R, int... C>
+__device__ __forceinline__ void dcanon(const R* q, R* dv, std::integer_sequence<int, C...>) {
+  ((dv[C] = dsum<l, DCanon<l, C>::t0>(q, std::make_integer_sequence<int, DCanon<l, C>::t1 - DCanon<l, C>::t0>{})),
+   ...);
+}
+template <int L, int l, typename R>
+__device__ __forceinline__ void dmatrix(const Geom<L, R>& g, R* dv) {
+  R q[2 * l + 1];
+#pragma unroll
+  for (int j = 0; j <= 2 * l; ++j) q[j] = g.cp[2 * l - j] * g.sp[j];
+  dcanon<l, R>(q, dv, std::make_integer_sequence<int, DCount<l>::ncanon>{});
+}
+
+// row index of (l, m) inside one polarisation block
+template <int l, int m>
+struct Row {
+  static constexpr int r = l * (l + 1) - 1 + m;
+};
+
+// ---- step 2: x'[l, MU] = sum_M R_{MU,M} e^{i M phi} x[l, M] ----------------
+// x~ (rotated about z) of degree l held in xt[2][2l+1][2]
+template <int L, int l, int MU, typename R, typename XV, int... MI>
+__device__ __forceinline__ void rot_fwd_row(const R* dv, const R (&xt)[2][2 * l + 1][2], XV& xp,
+                                            std::integer_sequence<int, MI...>) {
+  constexpr int NH = L * (L + 2);
+  R a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+  (
+      [&] {
+        constexpr int M = MI - l;
+        using RA = RAt<l, MU, M>;
+        const R w = RA::sign > 0 ? dv[RA::id] : -dv[RA::id];
+        a0 = fma_(w, xt[0][MI][0], a0);
+        a1 = fma_(w, xt[0][MI][1], a1);
+        b0 = fma_(w, xt[1][MI][0], b0);
+        b1 = fma_(w, xt[1][MI][1], b1);
+      }(),
+      ...);
+  constexpr int r = Row<l, MU>::r;
+  xp(2 * r) = a0;
+  xp(2 * r + 1) = a1;
+  xp(2 * (NH + r)) = b0;
+  xp(2 * (NH + r) + 1) = b1;
+}
+
+template <int L, int l, typename R, typename XV, int... MUI>
+__device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
+                                              std::integer_sequence<int, MUI...>) {
+  constexpr int NH = L * (L + 2);
+  R dv[DCount<l>::ncanon];
+  dmatrix<L, l>(g, dv);
+  R xt[2][2 * l + 1][2];
+#pragma unroll
+  for (int mi = 0; mi <= 2 * l; ++mi) {
+    const int m = mi - l;
+    const int am = m < 0 ? -m : m;
+    const R er = g.ere[am];
+    const R ei = m < 0 ? -g.eim[am] : g.eim[am];
+    const int r = l * (l + 1) - 1 + m;
+    const Pair2<R> xa = xs[r], xb = xs[NH + r];
+    xt[0][mi][0] = fma_(xa.re, er, -xa.im * ei);
+    xt[0][mi][1] = fma_(xa.re, ei, xa.im * er);
+    xt[1][mi][0] = fma_(xb.re, er, -xb.im * ei);
+    xt[1][mi][1] = fma_(xb.re, ei, xb.im * er);
+  }
+  (rot_fwd_row<L, l, MUI - l>(dv, xt, xp, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
+}
+
+template <int L, typename R, typename XV, int... LI>
+__device__ __forceinline__ void rot_fwd(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
+                                        std::integer_sequence<int, LI...>) {
+  (rot_fwd_block<L, LI + 1>(g, xs, xp, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+}
+
+// ---- step 3: axial translation --------------------------------------------
+template <int L, int MU, int LO, int LI, int T, typename R>
+__device__ __forceinline__ void ax_a(const Geom<L, R>& g, R& ar, R& ai) {
+  using A = AxialA<L, MU, LO, LI, T>;
+  constexpr R C = static_cast<R>(A::c);
+  ar = fma_(C, g.hre[A::p], ar);
+  ai = fma_(C, g.him[A::p], ai);
+}
+template <int L, int MU, int LO, int LI, int T, typename R>
+__device__ __forceinline__ void ax_b(const Geom<L, R>& g, R& br, R& bi) {
+  using B = AxialB<L, MU, LO, LI, T>;
+  constexpr R C = static_cast<R>(B::c);
+  br = fma_(C, g.hre[B::p], br);
+  bi = fma_(C, g.him[B::p], bi);
+}
+template <int L, int MU, int LO, int LI, typename R, int... KA, int... KB>
+__device__ __forceinline__ void ax_entry(const Geom<L, R>& g, R& ar, R& ai, R& br, R& bi,
+                                         std::integer_sequence<int, KA...>, std::integer_sequence<int, KB...>) {
+  (ax_a<L, MU, LO, LI, KA>(g, ar, ai), ...);
+  (ax_b<L, MU, LO, LI, KB>(g, br, bi), ...);
+}
+
+template <typename R>
+__device__ __forceinline__ void cmac(R& yr, R& yi, R wr, R wi, R xr, R xi) {
+  yr = fma_(wr, xr, fma_(-wi, xi, yr));
+  yi = fma_(wr, xi, fma_(wi, xr, yi));
+}
+
+// one (l, l') entry of the axial block for +MU (and the mirrored -MU),
+// accumulated into the row sums y[0..3] (+MU: y+ re/im, y- re/im) and
+// y[4..7] (-MU)
+template <int L, int MU, int LO, int LI, typename R, typename XV>
+__device__ __forceinline__ void ax_pair(const Geom<L, R>& g, XV& xp, R (&y)[8]) {
+  constexpr int NH = L * (L + 2);
+  if constexpr (LI >= MU) {
+    R ar = 0, ai = 0, br = 0, bi = 0;
+    ax_entry<L, MU, LO, LI>(g, ar, ai, br, bi, std::make_integer_sequence<int, AxialN<L, MU, LO, LI>::na>{},
+                            std::make_integer_sequence<int, AxialN<L, MU, LO, LI>::nb>{});
+    // W+ = A + i B', W- = A - i B'
+    const R wpr = ar - bi, wpi = ai + br, wmr = ar + bi, wmi = ai - br;
+    constexpr int ri = Row<LI, MU>::r;
+    cmac(y[0], y[1], wpr, wpi, xp(2 * ri), xp(2 * ri + 1));
+    cmac(y[2], y[3], wmr, wmi, xp(2 * (NH + ri)), xp(2 * (NH + ri) + 1));
+    if constexpr (MU > 0) {
+      // -mu: B changes sign, so W+ and W- swap
+      constexpr int rim = Row<LI, -MU>::r;
+      cmac(y[4], y[5], wmr, wmi, xp(2 * rim), xp(2 * rim + 1));
+      cmac(y[6], y[7], wpr, wpi, xp(2 * (NH + rim)), xp(2 * (NH + rim) + 1));
+    }
+  }
+}
+
+template <int L, int MU, int LO, typename R, typename XV, typename YV, int... LII>
+__device__ __forceinline__ void ax_row(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, LII...>) {
+  constexpr int NH = L * (L + 2);
+  if constexpr (LO >= MU) {
+    R y[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    (ax_pair<L, MU, LO, LII + 1>(g, xp, y), ...);
+    constexpr int ro = Row<LO, MU>::r;
+    yp(2 * ro) = y[0];
+    yp(2 * ro + 1) = y[1];
+    yp(2 * (NH + ro)) = y[2];
+    yp(2 * (NH + ro) + 1) = y[3];
+    if constexpr (MU > 0) {
+      constexpr int rom = Row<LO, -MU>::r;
+      yp(2 * rom) = y[4];
+      yp(2 * rom + 1) = y[5];
+      yp(2 * (NH + rom)) = y[6];
+      yp(2 * (NH + rom) + 1) = y[7];
+    }
+  }
+}
+template <int L, int MU, typename R, typename XV, typename YV, int... LOI>
+__device__ __forceinline__ void ax_mu(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, LOI...>) {
+  (ax_row<L, MU, LOI + 1>(g, xp, yp, std::make_integer_sequence<int, L>{}), ...);
+}
+template <int L, typename R, typename XV, typename YV, int... MUS>
+__device__ __forceinline__ void axial(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, MUS...>) {
+  (ax_mu<L, MUS>(g, xp, yp, std::make_integer_sequence<int, L>{}), ...);
+}
+
+// ---- step 4: y[l, M] += e^{-i M phi} sum_MU R_{MU,M} y'[l, MU] -------------
+template <int L, int l, int M, typename R, typename YV, typename Acc, int... MUI>
+__device__ __forceinline__ void rot_bwd_col(const Geom<L, R>& g, const R* dv, YV& yp, Acc& acc,
+                                            std::integer_sequence<int, MUI...>) {
+  constexpr int NH = L * (L + 2);
+  R a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+  (
+      [&] {
+        constexpr int MU = MUI - l;
+        using RA = RAt<l, MU, M>;
+        const R w = RA::sign > 0 ? dv[RA::id] : -dv[RA::id];
+        constexpr int r = Row<l, MU>::r;
+        a0 = fma_(w, yp(2 * r), a0);
+        a1 = fma_(w, yp(2 * r + 1), a1);
+        b0 = fma_(w, yp(2 * (NH + r)), b0);
+        b1 = fma_(w, yp(2 * (NH + r) + 1), b1);
+      }(),
+      ...);
+  constexpr int AM = M < 0 ? -M : M;
+  const R er = g.ere[AM];
+  const R ei = M < 0 ? g.eim[AM] : -g.eim[AM];  // e^{-i M phi}
+  constexpr int r = Row<l, M>::r;
+  R& c0 = acc(2 * r);
+  R& c1 = acc(2 * r + 1);
+  c0 = fma_(a0, er, fma_(-a1, ei, c0));
+  c1 = fma_(a0, ei, fma_(a1, er, c1));
+  R& d0 = acc(2 * (NH + r));
+  R& d1 = acc(2 * (NH + r) + 1);
+  d0 = fma_(b0, er, fma_(-b1, ei, d0));
+  d1 = fma_(b0, ei, fma_(b1, er, d1));
+}
+
+template <int L, int l, typename R, typename YV, typename Acc, int... MI>
+__device__ __forceinline__ void rot_bwd_block(const Geom<L, R>& g, YV& yp, Acc& acc,
+                                              std::integer_sequence<int, MI...>) {
+  R dv[DCount<l>::ncanon];
+  dmatrix<L, l>(g, dv);
+  (rot_bwd_col<L, l, MI - l>(g, dv, yp, acc, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
+}
+
+template <int L, typename R, typename YV, typename Acc, int... LI>
+__device__ __forceinline__ void rot_bwd(const Geom<L, R>& g, YV& yp, Acc& acc, std::integer_sequence<int, LI...>) {
+  (rot_bwd_block<L, LI + 1>(g, yp, acc, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+}
+
+// storage views: registers (compile-time index) or a per-thread column of a
+// shared-memory array [4 NH][BLOCK]
+template <typename R>
+struct AccReg {
+  R* a;
+  __device__ __forceinline__ R& operator()(int q) const { return a[q]; }
+};
+template <typename R, int BLOCK>
+struct AccSmem {
+  R* a;
+  __device__ __forceinline__ R& operator()(int q) const { return a[q * BLOCK]; }
+};
+
+template <int L, typename R, typename XV, typename YV, typename Acc>
+__device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, YV& yp, Acc& acc) {
+  rot_fwd<L>(g, xs, xp, std::make_integer_sequence<int, L>{});
+  axial<L>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
+  rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
+}
+
+template <int L, typename R>
+struct Config {
+  static constexpr bool FP64 = sizeof(R) == 8;
+  static constexpr int BLOCK = (FP64 && L >= 5) ? 32 : ((FP64 || L >= 5) ? 64 : 128);
+  static constexpr int TJ = FP64 ? 16 : 32;
+  static constexpr bool ACC_SMEM = FP64 ? (L >= 2) : (L >= 4);
+  static constexpr bool XY_SMEM = FP64 ? (L >= 3) : (L >= 5);
+};
+
+template <int L, typename R>
+struct Layout {
+  using C = Config<L, R>;
+  static constexpr int NH = L * (L + 2);
+  static constexpr size_t col = sizeof(R) * 4 * NH * C::BLOCK;  // one [4 NH][BLOCK] array
+  static constexpr size_t off_pos = 0;
+  static constexpr size_t off_x = off_pos + sizeof(Pos4) * C::TJ;
+  static constexpr size_t off_acc = off_x + sizeof(Pair2<R>) * 2 * NH * C::TJ;
+  static constexpr size_t off_xy = off_acc + (C::ACC_SMEM ? col : 0);
+  static constexpr size_t bytes = off_xy + (C::XY_SMEM ? 2 * col : 0);
+};
+
+// grid (receiver blocks of BLOCK, source chunks); writes partial sums in the
+// +- basis, [chunks][N][2][NH] complex (same layout as the direct kernel)
+template <int L, typename R>
+__global__ void __launch_bounds__(Config<L, R>::BLOCK)
+    rtr_partial_kernel(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
+                       Pair2<R>* __restrict__ partial, double k, int chunk) {
+  using C = Config<L, R>;
+  using LY = Layout<L, R>;
+  constexpr int NH = L * (L + 2);
+  constexpr int BLOCK = C::BLOCK;
+  constexpr int TJ = C::TJ;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  Pos4* spos = reinterpret_cast<Pos4*>(smem_raw + LY::off_pos);
+  Pair2<R>* sx = reinterpret_cast<Pair2<R>*>(smem_raw + LY::off_x);
+  R* sacc = reinterpret_cast<R*>(smem_raw + LY::off_acc);
+  R* sxy = reinterpret_cast<R*>(smem_raw + LY::off_xy);
+
+  const int tid = threadIdx.x;
+  const int i = blockIdx.x * BLOCK + tid;
+  const int j0 = blockIdx.y * chunk;
+  const int j1 = min(N, j0 + chunk);
+  const bool active = i < N;
+  Pos4 ri = Pos4{0, 0, 0, 0};
+  if (active) ri = pos[i];
+
+  R areg[C::ACC_SMEM ? 1 : 4 * NH];
+  if constexpr (C::ACC_SMEM) {
+    for (int q = 0; q < 4 * NH; ++q) sacc[q * BLOCK + tid] = static_cast<R>(0);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4 * NH; ++q) areg[q] = static_cast<R>(0);
+  }
+
+  for (int jt = j0; jt < j1; jt += TJ) {
+    const int nj = min(TJ, j1 - jt);
+    __syncthreads();
+    for (int q = tid; q < nj * NH; q += BLOCK) {
+      const int jj = q / NH;
+      const int r = q - jj * NH;
+      const Pair2<R> a = x[(size_t)(jt + jj) * (2 * NH) + r];
+      const Pair2<R> b = x[(size_t)(jt + jj) * (2 * NH) + NH + r];
+      sx[jj * 2 * NH + r] = Pair2<R>{a.re + b.re, a.im + b.im};
+      sx[jj * 2 * NH + NH + r] = Pair2<R>{a.re - b.re, a.im - b.im};
+    }
+    for (int q = tid; q < nj; q += BLOCK) spos[q] = pos[jt + q];
+    __syncthreads();
+    if (active) {
+      for (int jj = 0; jj < nj; ++jj) {
+        if (jt + jj == i) continue;  // no self coupling
+        const Pos4 rj = spos[jj];
+        Geom<L, R> g;
+        geometry<L, R>(ri.x - rj.x, ri.y - rj.y, ri.z - rj.z, k, g);
+        const Pair2<R>* xs = sx + jj * 2 * NH;
+        auto run = [&](auto& xp, auto& yp) {
+          if constexpr (C::ACC_SMEM) {
+            AccSmem<R, BLOCK> acc{sacc + tid};
+            pair<L, R>(g, xs, xp, yp, acc);
+          } else {
+            AccReg<R> acc{areg};
+            pair<L, R>(g, xs, xp, yp, acc);
+          }
+        };
+        if constexpr (C::XY_SMEM) {
+          AccSmem<R, BLOCK> xp{sxy + tid};
+          AccSmem<R, BLOCK> yp{sxy + 4 * NH * BLOCK + tid};
+          run(xp, yp);
+        } else {
+          R xa[4 * NH], ya[4 * NH];
+          AccReg<R> xp{xa};
+          AccReg<R> yp{ya};
+          run(xp, yp);
+        }
+      }
+    }
+  }
+  if (active) {
+    R* out = reinterpret_cast<R*>(partial + ((size_t)blockIdx.y * N + i) * (2 * NH));
+    if constexpr (C::ACC_SMEM) {
+      for (int q = 0; q < 4 * NH; ++q) out[q] = sacc[q * BLOCK + tid];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4 * NH; ++q) out[q] = areg[q];
+    }
+  }
+}
+
+template <int L, typename R>
+cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
+                           cudaStream_t st) {
+  using C = Config<L, R>;
+  using LY = Layout<L, R>;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(rtr_partial_kernel<L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(LY::bytes));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (N <= 0) return cudaSuccess;
+  if (chunks < 1) chunks = 1;
+  const int64_t chunk = (N + chunks - 1) / chunks;
+  dim3 grid(static_cast<unsigned>((N + C::BLOCK - 1) / C::BLOCK), static_cast<unsigned>(chunks));
+  rtr_partial_kernel<L, R><<<grid, C::BLOCK, LY::bytes, st>>>(static_cast<int>(N), static_cast<const Pos4*>(pos),
+                                                               static_cast<const Pair2<R>*>(x),
+                                                               static_cast<Pair2<R>*>(partial), k,
+                                                               static_cast<int>(chunk));
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rtr
+}  // namespace celes
+
+namespace celes {
+namespace rtr {
+static_assert(Layout<5, float>::bytes <= 227 * 1024, "shared memory of the lmax 5 FP32 kernel");
+static_assert(Layout<5, double>::bytes <= 227 * 1024, "shared memory of the lmax 5 FP64 kernel");
+static_assert(Layout<4, float>::bytes <= 227 * 1024, "shared memory of the lmax 4 FP32 kernel");
+}  // namespace rtr
+}  // namespace celes

@@ -98,10 +98,11 @@ def test_gaussian_beam_coefficients():
         B.celes_destroy(ctx)
 
 
+@pytest.mark.parametrize("kernel", [B.CELES_KERNEL_RTR, B.CELES_KERNEL_DIRECT])
 @pytest.mark.parametrize("N,L,poly,n", CLUSTERS)
-def test_coupling_and_master_matvec(N, L, poly, n):
+def test_coupling_and_master_matvec(N, L, poly, n, kernel):
     sc = synth.random_cluster(23, N + L, N, L, radius=100.0, fill=0.25, n=n, polydisperse=poly)
-    ctx = make_ctx(sc)
+    ctx = make_ctx(sc, kernel=kernel)
     try:
         W = translation.coupling_matrix(sc.positions, sc.k, L)
         t = mie.t_diagonal(L, sc.k, sc.radii, sc.n_rel)
@@ -129,8 +130,9 @@ def test_multi_rhs_matvec_and_chunking():
     W = translation.coupling_matrix(sc.positions, sc.k, 3)
     x = synth.random_vector(24, 1, (3, sc.N, sc.nmax))
     ref = np.stack([(W @ x[r].reshape(-1)).reshape(sc.N, sc.nmax) for r in range(3)])
-    for chunks in (0, 1, 3, 7):
-        ctx = make_ctx(sc, chunks=chunks)
+    for chunks, kernel in ((0, B.CELES_KERNEL_AUTO), (1, B.CELES_KERNEL_RTR), (3, B.CELES_KERNEL_DIRECT),
+                           (7, B.CELES_KERNEL_RTR)):
+        ctx = make_ctx(sc, chunks=chunks, kernel=kernel)
         try:
             assert rel(gpu_matvec(ctx, x, B.CELES_FP64, nrhs=3), ref) < 1e-10
             assert rel(gpu_matvec(ctx, x, B.CELES_FP32, nrhs=3), ref) < 1e-5
@@ -250,16 +252,22 @@ def test_full_size_config2_sampled_rows():
     on-the-fly rows."""
     sc = synth.config2(0)
     ctx = make_ctx(sc)
+    ctx_d = make_ctx(sc, kernel=B.CELES_KERNEL_DIRECT)
     try:
         x = synth.random_vector(2, 77, (sc.N, sc.nmax))
         y64 = gpu_matvec(ctx, x, B.CELES_FP64)
         y32 = gpu_matvec(ctx, x, B.CELES_FP32)
+        y32d = gpu_matvec(ctx_d, x, B.CELES_FP32)
         rows = list(np.random.default_rng(5).choice(sc.N, 8, replace=False))
         ref = translation.coupling_matvec_rows(sc.positions, sc.k, sc.lmax, x, rows)
         assert rel(y64[rows], ref) < 1e-10
         assert rel(y32[rows], ref) < 1e-5
+        assert rel(y32d[rows], ref) < 1e-5
+        # the two FP32 kernels agree on every receiver
+        assert rel(y32, y64) < 1e-5 and rel(y32d, y64) < 1e-5
     finally:
         B.celes_destroy(ctx)
+        B.celes_destroy(ctx_d)
 
 
 def test_overlap_and_argument_errors():
