@@ -50,7 +50,8 @@ typedef enum {
   CELES_ENUMERIC = -5,  /* NaN/Inf or breakdown detected */
   CELES_EOVERLAP = -6,  /* two spheres overlap (|r_i - r_j| < R_i + R_j) */
   CELES_ETIMEOUT = -7,  /* a bounded device wait gave up */
-  CELES_ESTATE = -8     /* call out of order (e.g. solve before set_incident) */
+  CELES_ESTATE = -8,    /* call out of order (e.g. solve before set_incident) */
+  CELES_ETOOBIG = -9    /* problem larger than a fixed-size buffer allows */
 } celes_status;
 
 typedef enum { CELES_FP64 = 0, CELES_FP32 = 1 } celes_precision;
@@ -211,6 +212,33 @@ int64_t celes_kernel_launches(void);
  * nmax^2; the rotation-translation-rotation variant counts its own rotations,
  * Wigner-d sums, axial build/apply and phases.  Host-only; -1 on bad lmax. */
 double celes_flops_per_pair(int lmax, int kernel);
+
+/* Coupling matvec y = W x that allocates no device memory (the paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code running under a host application's own device-memory pool,
+ * where direct allocations are forbidden, and latency-critical code that
+ * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree).
+ * It needs no context: the caller passes everything in its own device memory.
+ *   positions4 : device pointer to [N][4] doubles (x, y, z, unused), 32-byte
+ *                aligned
+ *   k          : background wavenumber n0 * k0
+ *   x, y       : device pointers to [N][nmax] complex128 (CELES_FP64) or
+ *                complex64 (CELES_FP32); one right-hand side; must not overlap
+ *   stream     : cudaStream_t as void* (NULL = the default stream)
+ * The kernel's scratch (its per-chunk partial sums) lives in one static
+ * 32 MiB device array compiled into the library, which every GPU that loads
+ * the library holds until the process exits.  Sizes whose single partial sum
+ * N * nmax * (16 or 8 bytes) exceeds 32 MiB return CELES_ETOOBIG before any GPU
+ * work (e.g. lmax 4: N <= 87381 in FP32, N <= 43690 in FP64).  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and sets the kernel's shared-memory attribute; make that first call before
+ * any stream capture.  The array holds the previous call's partial sums; every
+ * call overwrites all of the part it reads, so nothing needs clearing.  All
+ * calls share the one array, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them.  Stream ordered, no
+ * synchronisation; uses the rotation-translation-rotation kernel. */
+int celes_coupling_matvec_noalloc(int64_t N, int lmax, double k, const double* positions4, const void* x, void* y,
+                                  int precision, void* stream);
 
 void celes_destroy(celes_ctx* ctx);
 const char* celes_last_error(const celes_ctx* ctx);

@@ -24,8 +24,10 @@ CELES_ENUMERIC = -5
 CELES_EOVERLAP = -6
 CELES_ETIMEOUT = -7
 CELES_ESTATE = -8
+CELES_ETOOBIG = -9
 STATUS_NAMES = {0: "CELES_OK", -1: "CELES_EINVAL", -2: "CELES_ENOMEM", -3: "CELES_ECUDA", -4: "CELES_ENOCONV",
-                -5: "CELES_ENUMERIC", -6: "CELES_EOVERLAP", -7: "CELES_ETIMEOUT", -8: "CELES_ESTATE"}
+                -5: "CELES_ENUMERIC", -6: "CELES_EOVERLAP", -7: "CELES_ETIMEOUT", -8: "CELES_ESTATE",
+                -9: "CELES_ETOOBIG"}
 
 CELES_FP64 = 0
 CELES_FP32 = 1
@@ -99,6 +101,9 @@ SIGNATURES = [
     ("celes_kernel_time", ctypes.c_int, [_c_ctx_p, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]),
     ("celes_kernel_launches", ctypes.c_int64, []),
     ("celes_flops_per_pair", ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
+    ("celes_coupling_matvec_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_int, ctypes.c_void_p]),
     ("celes_destroy", None, [_c_ctx_p]),
     ("celes_last_error", ctypes.c_char_p, [_c_ctx_p]),
     ("celes_version", ctypes.c_char_p, []),
@@ -314,6 +319,17 @@ def celes_kernel_launches():
 
 def celes_flops_per_pair(lmax, kernel=CELES_KERNEL_AUTO):
     return float(load().celes_flops_per_pair(int(lmax), int(kernel)))
+
+
+def celes_coupling_matvec_noalloc(N, lmax, k, positions4, x, y, precision=CELES_FP64, stream=None,
+                                  check=True):
+    """y = W x without any device allocation by the library (see include/celes.h).
+    positions4, x, y: device buffers ([N][4] float64, [N][nmax] complex)."""
+    code = load().celes_coupling_matvec_noalloc(int(N), int(lmax), float(k), _devptr(positions4), _devptr(x),
+                                                 _devptr(y), int(precision), _stream(stream))
+    if check and code != CELES_OK:
+        raise CelesError(code, "celes_coupling_matvec_noalloc")
+    return code
 
 
 def celes_destroy(ctx):
