@@ -125,7 +125,8 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("coupling_kernel.cuh", "coupling_tables.cuh", "coupling_launch.cuh"):
+    for f in ("coupling_kernel.cuh", "coupling_tables.cuh", "coupling_launch.cuh", "rtr_kernel.cuh",
+              "rtr_tables.cuh"):
         with open(os.path.join(ROOT, "paper_1706_02145_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -200,7 +201,7 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"config2: {scene.N} polydisperse spheres, lmax {scene.lmax}, cylinder slab "
+            "config": {"workload": f"Gaussian-beam slab: {scene.N} polydisperse spheres, lmax {scene.lmax}, cylinder slab "
                                    "fill 0.3, Gaussian beam w=2um", "N": scene.N, "lmax": scene.lmax},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -374,7 +375,7 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         cores = host_cores()
-        rows = args.cpu_rows or max(cores, 8)
+        rows = args.cpu_rows or 8 * max(cores, 2)  # about 10 s of oracle work
         sel = list(np.random.default_rng(7).choice(N, rows, replace=False))
         rate, dt = cpu_oracle_rate(scene, sel, cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -385,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": f"config2: {N} polydisperse spheres (lognormal R, mean 150 nm), lmax {L}, "
+                "config": {"workload": f"Gaussian-beam slab: {N} polydisperse spheres (lognormal R, mean 150 nm), lmax {L}, "
                                        "n=1.5+0.001i, lambda 550 nm, cylinder slab fill 0.3, Gaussian beam w=2um; "
                                        "step = incident coefficients + FP32/FP64-refined GMRES to 1e-6 + far field",
                            "N": N, "lmax": L, "tol": TOL, "parallelism": "replicas" if world > 1 else "single GPU",

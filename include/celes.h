@@ -97,7 +97,8 @@ typedef enum {
 typedef enum {
   CELES_X0_TA = 0,     /* initial guess T a_in */
   CELES_X0_USER = 1,   /* guess given by celes_set_initial_guess */
-  CELES_X0_ZERO = 2
+  CELES_X0_ZERO = 2,
+  CELES_X0_LEARNED = 3 /* guess from celes_gnn_predict, used only where its residual is below that of T a_in */
 } celes_x0_kind;
 
 typedef struct {
@@ -121,6 +122,7 @@ typedef struct {
   double* history;          /* optional caller buffer for the residual history */
   int history_cap;          /* its capacity */
   int history_len;          /* entries written */
+  int guess_used;           /* RHS that started from the user / learned guess */
 } celes_solve_info;
 
 /* Create a context: copies positions [N][3], radii [N] and the complex
@@ -212,6 +214,46 @@ int64_t celes_kernel_launches(void);
  * nmax^2; the rotation-translation-rotation variant counts its own rotations,
  * Wigner-d sums, axial build/apply and phases.  Host-only; -1 on bad lmax. */
 double celes_flops_per_pair(int lmax, int kernel);
+
+/* Tensor-core GEMM C = alpha A B^T + beta C (the dense layers of the learned
+ * initial guess; the paper has no counterpart).  A: [M][K] BF16, B: [N][K]
+ * BF16 (row-major, K contiguous, lda/ldb in elements), C: [M][N] FP32
+ * (row-major, ldc).  Device pointers; K, lda, ldb multiples of 8 and A, B
+ * 16-byte aligned (else CELES_EINVAL).  Runs tcgen05.mma (kind::f16, FP32
+ * accumulation in tensor memory) on sm_103a; synchronises the stream and
+ * returns CELES_ETIMEOUT if a bounded wait on the tensor core gave up. */
+int celes_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc, float alpha,
+                    float beta, void* stream);
+
+/* Learned initial guess (Sec. 4.2: the solver accepts a custom initial
+ * condition).  A graph network over each sphere's 16 nearest neighbours
+ * (relative positions in wavelengths, k R_i, n_i, the scaled T a_in of the
+ * sphere) predicts d_i = b_i - (T a_in)_i; the first iterate is T a_in + d.
+ * Layers: input 1 dense, `layers` message-passing rounds (message MLP on
+ * [h_j; h_i; e_ij], mean aggregation, residual update MLP), output dense; all
+ * dense layers run on the tcgen05 BF16 GEMM with FP32 accumulation, and
+ * training (MSE, Adam) uses hand-written backward kernels.
+ *   celes_gnn_create : width (multiple of 16, <= 512), layers (1..8), knn = 16;
+ *                      the output layer starts at zero (untrained guess = T a)
+ *   celes_gnn_train  : `steps` Adam steps on one solved context (its current
+ *                      solution b of RHS `rhs` is the target); loss_out gets
+ *                      the last MSE (scaled units); CELES_ESTATE if unsolved
+ *   celes_gnn_predict: computes the guess for every RHS of a context and
+ *                      stores it for celes_solve with x0 = CELES_X0_LEARNED
+ * The paper has no counterpart of the network itself; the final FP64 residual
+ * of the solve judges it, and celes_solve falls back to T a_in per RHS. */
+typedef struct celes_gnn celes_gnn;
+int celes_gnn_create(celes_gnn** out, int lmax, int width, int layers, int knn, uint64_t seed, int device);
+int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps, double lr, double* loss_out);
+int celes_gnn_predict(celes_gnn* g, celes_ctx* ctx);
+int celes_gnn_num_params(const celes_gnn* g);
+/* Copy the parameters (what = 0) or the gradients of the last training pass
+ * (what = 1) to `host` as FP32, layer by layer (input, then message and update
+ * of each round, then output), each layer as its weight [out][in] row-major
+ * followed by its bias [out].  host = NULL returns the count.  celes_gnn_train
+ * with steps = 0 computes the loss and gradients without updating. */
+int celes_gnn_export(celes_gnn* g, int what, float* host, int cap);
+void celes_gnn_destroy(celes_gnn* g);
 
 /* Coupling matvec y = W x that allocates no device memory (the paper has no
  * counterpart; this entry point exists for callers that cannot call

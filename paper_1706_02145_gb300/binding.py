@@ -38,6 +38,7 @@ CELES_SOLVE_MIXED = 1
 CELES_X0_TA = 0
 CELES_X0_USER = 1
 CELES_X0_ZERO = 2
+CELES_X0_LEARNED = 3
 
 
 CELES_KERNEL_AUTO = 0
@@ -67,7 +68,7 @@ class celes_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer", ctypes.c_int),
                 ("matvecs_fp64", ctypes.c_int), ("matvecs_fp32", ctypes.c_int), ("residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int)]
+                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int), ("guess_used", ctypes.c_int)]
 
 
 _c_ctx_p = ctypes.c_void_p
@@ -104,6 +105,17 @@ SIGNATURES = [
     ("celes_coupling_matvec_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                      ctypes.c_int, ctypes.c_void_p]),
+    ("celes_gemm_bf16", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_void_p]),
+    ("celes_gnn_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_uint64, ctypes.c_int]),
+    ("celes_gnn_train", ctypes.c_int, [ctypes.c_void_p, _c_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]),
+    ("celes_gnn_predict", ctypes.c_int, [ctypes.c_void_p, _c_ctx_p]),
+    ("celes_gnn_num_params", ctypes.c_int, [ctypes.c_void_p]),
+    ("celes_gnn_export", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.c_int]),
+    ("celes_gnn_destroy", None, [ctypes.c_void_p]),
     ("celes_destroy", None, [_c_ctx_p]),
     ("celes_last_error", ctypes.c_char_p, [_c_ctx_p]),
     ("celes_version", ctypes.c_char_p, []),
@@ -236,7 +248,7 @@ def celes_solve(ctx, tol, mode=CELES_SOLVE_MIXED, restart=100, max_iter=2000, ma
     code = load().celes_solve(ctx, float(tol), ctypes.byref(opts), ctypes.byref(info))
     out = {"status": int(code), "iterations": info.iterations, "outer": info.outer,
            "matvecs_fp64": info.matvecs_fp64, "matvecs_fp32": info.matvecs_fp32, "residual": info.residual,
-           "seconds": info.seconds, "history": hist[:info.history_len].copy()}
+           "seconds": info.seconds, "history": hist[:info.history_len].copy(), "guess_used": info.guess_used}
     if code != CELES_OK and not (code == CELES_ENOCONV and not raise_on_noconv):
         _check(code, ctx)
     return out
@@ -330,6 +342,59 @@ def celes_coupling_matvec_noalloc(N, lmax, k, positions4, x, y, precision=CELES_
     if check and code != CELES_OK:
         raise CelesError(code, "celes_coupling_matvec_noalloc")
     return code
+
+
+def celes_gemm_bf16(A, B, C, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha A B^T + beta C on the tensor cores; A (M, K), B (N, K) bf16 CUDA tensors, C (M, N) float32."""
+    M, K = A.shape
+    N = B.shape[0]
+    code = load().celes_gemm_bf16(M, N, K, _devptr(A), A.stride(0), _devptr(B), B.stride(0), _devptr(C),
+                                  C.stride(0), float(alpha), float(beta), _stream(stream))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_gemm_bf16")
+    return C
+
+
+def celes_gnn_create(lmax, width=128, layers=3, knn=16, seed=0, device=0):
+    g = ctypes.c_void_p()
+    code = load().celes_gnn_create(ctypes.byref(g), int(lmax), int(width), int(layers), int(knn), int(seed),
+                                   int(device))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_gnn_create")
+    return g
+
+
+def celes_gnn_train(g, ctx, rhs=0, steps=1, lr=1e-3):
+    loss = ctypes.c_double(0.0)
+    code = load().celes_gnn_train(g, ctx, int(rhs), int(steps), float(lr), ctypes.byref(loss))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_gnn_train")
+    return loss.value
+
+
+def celes_gnn_predict(g, ctx):
+    return _check(load().celes_gnn_predict(g, ctx), ctx)
+
+
+def celes_gnn_num_params(g):
+    return int(load().celes_gnn_num_params(g))
+
+
+def celes_gnn_export(g, what=0):
+    lib = load()
+    n = lib.celes_gnn_export(g, int(what), None, 0)
+    if n < 0:
+        raise CelesError(n, "celes_gnn_export")
+    out = np.zeros(n, dtype=np.float32)
+    code = lib.celes_gnn_export(g, int(what), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
+    if code < 0:
+        raise CelesError(code, "celes_gnn_export")
+    return out
+
+
+def celes_gnn_destroy(g):
+    if g:
+        load().celes_gnn_destroy(g)
 
 
 def celes_destroy(ctx):

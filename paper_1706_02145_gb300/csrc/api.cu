@@ -150,7 +150,7 @@ struct celes_ctx {
   DevBuf pos, radii, nrel, tq, tq32, tdiag;
   int nrhs = 0;
   DevBuf ain, rhs, b, x0;
-  bool has_b = false, has_x0 = false;
+  bool has_b = false, has_x0 = false, x0_learned = false;
   DevBuf partial;
   // preconditioner
   bool has_precond = false;
@@ -845,6 +845,38 @@ struct Gmres {
 
 }  // namespace
 
+namespace celes {
+int ctx_view(celes_ctx* c, CtxView* v) {
+  if (!c || !v) return CELES_EINVAL;
+  v->N = c->N;
+  v->L = c->L;
+  v->nmax = c->nmax;
+  v->nrhs = c->nrhs;
+  v->k = c->k;
+  v->pos = c->pos.p;
+  v->radii = c->radii.as<double>();
+  v->nrel = c->nrel.as<double>();
+  v->rhs = c->rhs.as<double>();
+  v->b = c->b.as<double>();
+  v->has_b = c->has_b;
+  if (c->nrhs < 1) return CELES_ESTATE;
+  return CELES_OK;
+}
+
+int ctx_set_learned_guess(celes_ctx* c, int rhs, const double* b0_dev) {
+  if (!c || !b0_dev || rhs < 0 || rhs >= c->nrhs) return CELES_EINVAL;
+  DeviceGuard dg(c->device);
+  const size_t per = sizeof(double) * 2 * c->N * c->nmax;
+  CK(c->x0.ensure(per * c->nrhs), "x0");
+  if (!c->x0_learned) CK(cudaMemcpyAsync(c->x0.p, c->rhs.p, per * c->nrhs, cudaMemcpyDeviceToDevice, c->stream), "x0");
+  CK(cudaMemcpyAsync(c->x0.as<char>() + per * rhs, b0_dev, per, cudaMemcpyDeviceToDevice, c->stream), "x0");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  c->has_x0 = true;
+  c->x0_learned = true;
+  return CELES_OK;
+}
+}  // namespace celes
+
 extern "C" int celes_set_initial_guess(celes_ctx* c, const double* b0) {
   if (!c) return CELES_EINVAL;
   if (!b0) return fail(c, CELES_EINVAL, "set_initial_guess: null pointer");
@@ -854,6 +886,7 @@ extern "C" int celes_set_initial_guess(celes_ctx* c, const double* b0) {
   CK(c->x0.ensure(bytes), "x0");
   CK(cudaMemcpy(c->x0.p, b0, bytes, cudaMemcpyHostToDevice), "h2d");
   c->has_x0 = true;
+  c->x0_learned = false;
   return CELES_OK;
 }
 
@@ -870,13 +903,16 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
   if (opt.mode != CELES_SOLVE_FP64 && opt.mode != CELES_SOLVE_MIXED)
     return fail(c, CELES_EINVAL, "solve: unknown mode %d", opt.mode);
   if (opt.x0 == CELES_X0_USER && !c->has_x0) return fail(c, CELES_ESTATE, "solve: no user initial guess set");
+  if (opt.x0 == CELES_X0_LEARNED && !(c->has_x0 && c->x0_learned))
+    return fail(c, CELES_ESTATE, "solve: no learned guess (call celes_gnn_predict)");
+  if (opt.x0 < CELES_X0_TA || opt.x0 > CELES_X0_LEARNED) return fail(c, CELES_EINVAL, "solve: unknown x0 kind");
   DeviceGuard dg(c->device);
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = c->N * c->nmax;
   const size_t per64 = sizeof(double) * 2 * n;
   const bool use_pc = opt.use_precond && c->has_precond;
   std::vector<double> hist;
-  int total_its = 0, outer = 0, mv64 = 0, mv32 = 0;
+  int total_its = 0, outer = 0, mv64 = 0, mv32 = 0, guess_used = 0;
   double worst = 0.0;
   int status = CELES_OK;
   DevBuf r64, d64, r32, d32;
@@ -898,13 +934,45 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
     double* b = reinterpret_cast<double*>(c->b.as<char>() + per64 * rr);
     // initial guess
     if (opt.x0 == CELES_X0_TA) CK(cudaMemcpyAsync(b, rhs, per64, cudaMemcpyDeviceToDevice, c->stream), "x0");
-    else if (opt.x0 == CELES_X0_USER)
+    else if (opt.x0 == CELES_X0_USER || opt.x0 == CELES_X0_LEARNED)
       CK(cudaMemcpyAsync(b, c->x0.as<char>() + per64 * rr, per64, cudaMemcpyDeviceToDevice, c->stream), "x0");
     else CK(cudaMemsetAsync(b, 0, per64, c->stream), "x0");
     double rhs_norm = 0.0;
     {
       int s = g64.norm(rhs, rhs_norm);
       if (s) return s;
+    }
+    if (opt.x0 == CELES_X0_LEARNED) {
+      // keep the learned first iterate only if its residual is below that of
+      // T a_in (residuals in the precision of the solve's first residual)
+      const int pr = opt.mode == CELES_SOLVE_FP64 ? CELES_FP64 : CELES_FP32;
+      double rn[2] = {0.0, 0.0};
+      for (int cand = 0; cand < 2; ++cand) {
+        const double* xv = cand == 0 ? rhs : b;
+        if (pr == CELES_FP64) {
+          int s = coupling_apply(c, xv, r64.p, 1, CELES_FP64, 1, c->stream);
+          if (s) return s;
+          ++mv64;
+          CK(launch_axpby<double, double>(n, 1.0, rhs, -1.0, r64.p, c->stream), "residual");
+          s = g64.norm(r64.p, rn[cand]);
+          if (s) return s;
+        } else {
+          CK(launch_axpby<double, float>(n, 1.0, xv, 0.0, d32.p, c->stream), "cast");
+          int s = coupling_apply(c, d32.p, r32.p, 1, CELES_FP32, 1, c->stream);
+          if (s) return s;
+          ++mv32;
+          CK(launch_axpby<double, float>(n, 1.0, rhs, -1.0, r32.p, c->stream), "residual32");
+          s = g32.norm(r32.p, rn[cand]);
+          if (s) return s;
+        }
+      }
+      if (rn[1] < rn[0]) {
+        ++guess_used;
+      } else {
+        CK(cudaMemcpyAsync(b, rhs, per64, cudaMemcpyDeviceToDevice, c->stream), "x0");
+      }
+    } else if (opt.x0 == CELES_X0_USER) {
+      ++guess_used;
     }
     if (!(rhs_norm > 0.0)) {
       CK(cudaMemsetAsync(b, 0, per64, c->stream), "zero");
@@ -1001,6 +1069,7 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
     info->residual = worst;
     info->seconds = secs;
     info->history_len = 0;
+    info->guess_used = guess_used;
     if (info->history && info->history_cap > 0) {
       const int nh = std::min<int>(info->history_cap, static_cast<int>(hist.size()));
       std::memcpy(info->history, hist.data(), sizeof(double) * nh);

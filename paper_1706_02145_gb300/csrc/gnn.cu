@@ -1,0 +1,854 @@
+// Learned initial guess for the iterative solve (the paper's hook, Sec. 4.2:
+// "a custom initial condition"): a graph network over each sphere's K nearest
+// neighbours predicts the correction d_i = b_i - (T a_in)_i of the scattered
+// coefficients.  The solver uses T a_in + d as its first iterate and falls
+// back to T a_in if that residual is not smaller.
+//
+// Network (all dense layers on the tcgen05 BF16 GEMM, FP32 accumulation):
+//   h_i   = relu(W_in f_i + b_in)                       f_i: (T a)_i, k R_i, n_i
+//   layer l = 1..L:
+//     m_ij = relu(W_m [h_j ; h_i ; e_ij] + b_m)          j in the K nearest spheres
+//     a_i  = mean_j m_ij
+//     h_i  = h_i + relu(W_u [h_i ; a_i] + b_u)
+//   d_i   = W_o h_i + b_o                               (re, im of nmax coefficients)
+// e_ij: relative position in wavelengths, distance, 1 / (k d).
+// Training: MSE against (b - T a) of solved ensembles, Adam, hand-written
+// backward kernels.  Inputs and targets are scaled by 1 / rms(T a).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/celes.h"
+#include "coupling_kernel.cuh"
+#include "kernels.h"
+
+namespace celes {
+namespace gnn {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kEdgeFeat = 8;  // padded edge features
+
+static int round8(int x) { return (x + 7) / 8 * 8; }
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// K nearest neighbours by exhaustive search (insertion into a sorted list)
+template <int KN>
+__global__ void knn_kernel(int N, const Pos4* __restrict__ pos, int* __restrict__ nbr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float bd[KN];
+  int bi[KN];
+#pragma unroll
+  for (int q = 0; q < KN; ++q) {
+    bd[q] = 3.0e38f;
+    bi[q] = i;
+  }
+  const Pos4 p = pos[i];
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    const Pos4 r = pos[j];
+    const float dx = static_cast<float>(r.x - p.x), dy = static_cast<float>(r.y - p.y),
+                dz = static_cast<float>(r.z - p.z);
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 < bd[KN - 1]) {
+      int q = KN - 1;
+      while (q > 0 && bd[q - 1] > d2) {
+        bd[q] = bd[q - 1];
+        bi[q] = bi[q - 1];
+        --q;
+      }
+      bd[q] = d2;
+      bi[q] = j;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KN; ++q) nbr[(size_t)i * KN + q] = bi[q];
+}
+
+// node features [N][F] (bf16): scaled (T a)_i re/im, k R_i, Re n_rel - 1, Im n_rel, zero padding
+__global__ void node_features_kernel(int N, int nmax, int F, const double* __restrict__ ta,
+                                     const double* __restrict__ radii, const double* __restrict__ nrel, double k,
+                                     double scale, bf16* __restrict__ feat) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * F) return;
+  const int i = static_cast<int>(t / F), c = static_cast<int>(t % F);
+  float v = 0.0f;
+  if (c < 2 * nmax) v = static_cast<float>(ta[(size_t)i * 2 * nmax + c] * scale);
+  else if (c == 2 * nmax) v = static_cast<float>(k * radii[i]);
+  else if (c == 2 * nmax + 1) v = static_cast<float>(nrel[2 * i] - 1.0);
+  else if (c == 2 * nmax + 2) v = static_cast<float>(nrel[2 * i + 1]);
+  feat[t] = __float2bfloat16(v);
+}
+
+// edge features [E][8]: (r_j - r_i) k / 2pi, |d| k / 2pi, 1 / (k |d|), 0, 0, 0
+__global__ void edge_features_kernel(int N, int KN, const Pos4* __restrict__ pos, const int* __restrict__ nbr, double k,
+                                     float* __restrict__ ef) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)N * KN) return;
+  const int i = static_cast<int>(e / KN);
+  const int j = nbr[e];
+  const Pos4 a = pos[i], b = pos[j];
+  const double s = k / 6.283185307179586;
+  const double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+  const double d = sqrt(dx * dx + dy * dy + dz * dz);
+  float* o = ef + e * kEdgeFeat;
+  o[0] = static_cast<float>(dx * s);
+  o[1] = static_cast<float>(dy * s);
+  o[2] = static_cast<float>(dz * s);
+  o[3] = static_cast<float>(d * s);
+  o[4] = d > 0 ? static_cast<float>(1.0 / (k * d)) : 0.0f;
+  o[5] = o[6] = o[7] = 0.0f;
+}
+
+// target [N][2 nmax] (fp32) = (b - T a) * scale
+__global__ void target_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ ta, double scale,
+                              float* __restrict__ tgt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) tgt[t] = static_cast<float>((b[t] - ta[t]) * scale);
+}
+
+// edge input rows [E][2W + 8] bf16: [h_j ; h_i ; e_ij]
+__global__ void edge_input_kernel(int N, int KN, int W, const float* __restrict__ h, const int* __restrict__ nbr,
+                                  const float* __restrict__ ef, bf16* __restrict__ x) {
+  const int ld = 2 * W + kEdgeFeat;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * KN * ld) return;
+  const int64_t e = t / ld;
+  const int c = static_cast<int>(t % ld);
+  const int i = static_cast<int>(e / KN);
+  float v;
+  if (c < W) v = h[(size_t)nbr[e] * W + c];
+  else if (c < 2 * W) v = h[(size_t)i * W + (c - W)];
+  else v = ef[e * kEdgeFeat + (c - 2 * W)];
+  x[t] = __float2bfloat16(v);
+}
+
+// z += bias (per column); y = relu(z); optional bf16 copy of y
+__global__ void bias_relu_kernel(int64_t rows, int cols, float* __restrict__ z, const float* __restrict__ bias,
+                                 float* __restrict__ y, bf16* __restrict__ y16, int relu) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rows * cols) return;
+  const int c = static_cast<int>(t % cols);
+  const float v = z[t] + bias[c];
+  z[t] = v;
+  const float r = relu ? fmaxf(v, 0.0f) : v;
+  if (y) y[t] = r;
+  if (y16) y16[t] = __float2bfloat16(r);
+}
+
+// update input [N][2W] bf16: [h_i ; mean_j m_ij]; also stores the mean (fp32)
+__global__ void aggregate_kernel(int N, int KN, int W, const float* __restrict__ h, const float* __restrict__ m,
+                                 float* __restrict__ agg, bf16* __restrict__ u) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * W) return;
+  const int i = static_cast<int>(t / W), c = static_cast<int>(t % W);
+  float s = 0.0f;
+  for (int q = 0; q < KN; ++q) s += m[((size_t)i * KN + q) * W + c];
+  s *= 1.0f / KN;
+  agg[t] = s;
+  u[(size_t)i * 2 * W + c] = __float2bfloat16(h[t]);
+  u[(size_t)i * 2 * W + W + c] = __float2bfloat16(s);
+}
+
+// h += y (residual update)
+__global__ void add_kernel(int64_t n, float* __restrict__ h, const float* __restrict__ y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) h[t] += y[t];
+}
+
+// fp32 -> bf16
+__global__ void to_bf16_kernel(int64_t n, const float* __restrict__ x, bf16* __restrict__ y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) y[t] = __float2bfloat16(x[t]);
+}
+
+// out[c][r] = in[r][c] for r < rows (columns padded with zeros up to rpad), bf16 output
+template <typename T>
+__global__ void transpose_kernel(int rows, int cols, int rpad, const T* __restrict__ in, bf16* __restrict__ out) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + q, c = c0 + threadIdx.x;
+    float v = 0.0f;
+    if (r < rows && c < cols) v = static_cast<float>(in[(size_t)r * cols + c]);
+    tile[q][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int c = c0 + q, r = r0 + threadIdx.x;
+    if (c < cols && r < rpad) out[(size_t)c * rpad + r] = __float2bfloat16(tile[threadIdx.x][q]);
+  }
+}
+
+// loss = mean (o - t)^2 (partial sums per block) and grad = 2 (o - t) / n
+__global__ void mse_kernel(int64_t n, const float* __restrict__ o, const float* __restrict__ t, float* __restrict__ g,
+                           double* __restrict__ loss) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const float d = o[q] - t[q];
+    g[q] = 2.0f * d / static_cast<float>(n);
+    s += static_cast<double>(d) * d;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] / static_cast<double>(n));
+}
+
+// dz = dy * (z > 0)   (in place on dy), relu backward
+__global__ void relu_bwd_kernel(int64_t n, const float* __restrict__ z, float* __restrict__ dy) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n && z[t] <= 0.0f) dy[t] = 0.0f;
+}
+
+// column sums of dz [rows][cols] -> db [cols] (accumulated)
+__global__ void colsum_kernel(int64_t rows, int cols, const float* __restrict__ dz, float* __restrict__ db) {
+  const int c = blockIdx.x;
+  float s = 0.0f;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += dz[r * cols + c];
+  __shared__ float red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] += red[0];
+}
+
+// backward of the aggregation and the edge gather:
+//   dm_e = dagg_i / K       (dagg from the update input gradient, columns W..2W)
+__global__ void agg_bwd_kernel(int N, int KN, int W, const float* __restrict__ du, float* __restrict__ dm) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * KN * W) return;
+  const int64_t e = t / W;
+  const int c = static_cast<int>(t % W);
+  const int i = static_cast<int>(e / KN);
+  dm[t] = du[(size_t)i * 2 * W + W + c] * (1.0f / KN);
+}
+
+// dh_i += du[i][0:W]
+__global__ void dh_from_update_kernel(int N, int W, const float* __restrict__ du, float* __restrict__ dh) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * W) return;
+  const int i = static_cast<int>(t / W), c = static_cast<int>(t % W);
+  dh[t] += du[(size_t)i * 2 * W + c];
+}
+
+// scatter edge-input gradient: dh_j += dx_e[0:W], dh_i += dx_e[W:2W]   (one thread per node and column,
+// gathering the in-edges of j through the reverse lists)
+__global__ void edge_scatter_kernel(int N, int KN, int W, const float* __restrict__ dx, const int* __restrict__ rev_off,
+                                    const int* __restrict__ rev_edge, float* __restrict__ dh) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * W) return;
+  const int i = static_cast<int>(t / W), c = static_cast<int>(t % W);
+  const int ld = 2 * W + kEdgeFeat;
+  float s = 0.0f;
+  for (int q = 0; q < KN; ++q) s += dx[((size_t)i * KN + q) * ld + W + c];
+  for (int q = rev_off[i]; q < rev_off[i + 1]; ++q) s += dx[(size_t)rev_edge[q] * ld + c];
+  dh[t] += s;
+}
+
+// Adam step on fp32 master weights, refreshes the bf16 copy
+__global__ void adam_kernel(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
+                            float* __restrict__ m2, bf16* __restrict__ w16, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float gi = g[t];
+  const float a = b1 * m1[t] + (1.0f - b1) * gi;
+  const float b = b2 * m2[t] + (1.0f - b2) * gi * gi;
+  m1[t] = a;
+  m2[t] = b;
+  const float upd = lr * (a / c1) / (sqrtf(b / c2) + eps);
+  w[t] -= upd;
+  if (w16) w16[t] = __float2bfloat16(w[t]);
+}
+
+// guess b0 = T a + d / scale
+__global__ void guess_kernel(int64_t n, const double* __restrict__ ta, const float* __restrict__ o, double inv_scale,
+                             double* __restrict__ b0) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b0[t] = ta[t] + static_cast<double>(o[t]) * inv_scale;
+}
+
+__global__ void sumsq_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    s += x[q] * x[q];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+inline unsigned blocks(int64_t n, int t = 256) { return static_cast<unsigned>((n + t - 1) / t); }
+
+}  // namespace gnn
+}  // namespace celes
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace celes {
+int ctx_view(celes_ctx* c, CtxView* v);
+int ctx_set_learned_guess(celes_ctx* c, int rhs, const double* b0_dev);
+}  // namespace celes
+
+using namespace celes;
+using namespace celes::gnn;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (!bytes) return cudaSuccess;
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct Dense {
+  int out = 0, in = 0;  // weight [out][in]
+  Buf w, w16, wt16, g, m1, m2, b, gb, mb1, mb2;
+};
+
+}  // namespace
+
+struct celes_gnn {
+  int device = 0;
+  int lmax = 3, width = 128, layers = 3, knn = 16;
+  int nmax = 30, F = 64, OUTP = 64;
+  int64_t step = 0;
+  cudaStream_t stream = nullptr;
+  Dense in, out;
+  std::vector<std::unique_ptr<Dense>> msg, upd;
+  // graph / activations (sized for the largest N seen)
+  int64_t capN = 0;
+  Buf nbr, rev_off, rev_edge, ef, feat, tgt, zin, hin16;
+  std::vector<std::unique_ptr<Buf>> h, xe, zm, mm, agg, u, zu, yu;
+  Buf o, dout, dh, dh2, dzu, du, dm, dxe, t1, t2, t3, lossd, err, tmp16;
+  std::string errmsg;
+};
+
+namespace {
+
+#define GK(expr)                                  \
+  do {                                            \
+    const cudaError_t e_ = (expr);                \
+    if (e_ != cudaSuccess) return CELES_ECUDA;    \
+  } while (0)
+
+int dense_init(Dense& d, int out, int in, std::mt19937_64& rng, cudaStream_t st) {
+  d.out = out;
+  d.in = in;
+  const size_t n = (size_t)out * in;
+  GK(d.w.ensure(n * 4));
+  GK(d.w16.ensure(n * 2));
+  GK(d.wt16.ensure(n * 2));
+  GK(d.g.ensure(n * 4));
+  GK(d.m1.ensure(n * 4));
+  GK(d.m2.ensure(n * 4));
+  GK(d.b.ensure(out * 4));
+  GK(d.gb.ensure(out * 4));
+  GK(d.mb1.ensure(out * 4));
+  GK(d.mb2.ensure(out * 4));
+  std::vector<float> hw(n);
+  std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / in));
+  for (auto& x : hw) x = nd(rng);
+  GK(cudaMemcpyAsync(d.w.p, hw.data(), n * 4, cudaMemcpyHostToDevice, st));
+  GK(cudaMemsetAsync(d.m1.p, 0, n * 4, st));
+  GK(cudaMemsetAsync(d.m2.p, 0, n * 4, st));
+  GK(cudaMemsetAsync(d.b.p, 0, out * 4, st));
+  GK(cudaMemsetAsync(d.mb1.p, 0, out * 4, st));
+  GK(cudaMemsetAsync(d.mb2.p, 0, out * 4, st));
+  return CELES_OK;
+}
+
+// refresh the bf16 copies W and W^T
+int dense_sync16(Dense& d, cudaStream_t st) {
+  const int64_t n = (int64_t)d.out * d.in;
+  to_bf16_kernel<<<blocks(n), 256, 0, st>>>(n, d.w.as<float>(), d.w16.as<bf16>());
+  dim3 tb(32, 8), tg((d.in + 31) / 32, (d.out + 31) / 32);
+  transpose_kernel<float><<<tg, tb, 0, st>>>(d.out, d.in, d.out, d.w.as<float>(), d.wt16.as<bf16>());
+  note_launch(2);
+  GK(cudaGetLastError());
+  return CELES_OK;
+}
+
+int gemm(celes_gnn* g, int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+         float beta) {
+  GK(launch_gemm_bf16_tn(M, N, K, A, lda, B, ldb, C, ldc, 1.0f, beta, g->err.as<int>(), g->stream));
+  return CELES_OK;
+}
+
+// transpose rows x cols (float or bf16) into bf16 [cols][rpad]
+template <typename T>
+int transpose(celes_gnn* g, int rows, int cols, int rpad, const T* in, bf16* out) {
+  dim3 tb(32, 8), tg((cols + 31) / 32, (rpad + 31) / 32);
+  transpose_kernel<T><<<tg, tb, 0, g->stream>>>(rows, cols, rpad, in, out);
+  note_launch();
+  GK(cudaGetLastError());
+  return CELES_OK;
+}
+
+// dW += dZ^T X (X given as bf16 [rows][in] row-major), db += colsum(dZ)
+int dense_grad(celes_gnn* g, Dense& d, int rows, const float* dz, const bf16* x) {
+  const int rpad = round8(rows);
+  Buf& tA = g->t1;
+  Buf& tB = g->t2;
+  GK(tA.ensure((size_t)d.out * rpad * 2));
+  GK(tB.ensure((size_t)d.in * rpad * 2));
+  int s = transpose<float>(g, rows, d.out, rpad, dz, tA.as<bf16>());
+  if (s) return s;
+  s = transpose<bf16>(g, rows, d.in, rpad, x, tB.as<bf16>());
+  if (s) return s;
+  s = gemm(g, d.out, d.in, rpad, tA.p, rpad, tB.p, rpad, d.g.as<float>(), d.in, 1.0f);
+  if (s) return s;
+  colsum_kernel<<<d.out, 256, 0, g->stream>>>(rows, d.out, dz, d.gb.as<float>());
+  note_launch();
+  GK(cudaGetLastError());
+  return CELES_OK;
+}
+
+int ensure_capacity(celes_gnn* g, int64_t N) {
+  if (N <= g->capN) return CELES_OK;
+  const int W = g->width, KN = g->knn;
+  const int64_t E = N * KN;
+  const int XE = 2 * W + kEdgeFeat;
+  GK(g->nbr.ensure(E * 4));
+  GK(g->rev_off.ensure((N + 1) * 4));
+  GK(g->rev_edge.ensure(E * 4));
+  GK(g->ef.ensure(E * kEdgeFeat * 4));
+  GK(g->feat.ensure(N * g->F * 2));
+  GK(g->tgt.ensure(N * g->OUTP * 4));
+  GK(g->zin.ensure(N * W * 4));
+  GK(g->hin16.ensure(N * W * 2));
+  g->h.clear();
+  g->xe.clear();
+  g->zm.clear();
+  g->mm.clear();
+  g->agg.clear();
+  g->u.clear();
+  g->zu.clear();
+  g->yu.clear();
+  for (int l = 0; l <= g->layers; ++l) {
+    g->h.emplace_back(new Buf());
+    GK(g->h.back()->ensure(N * W * 4));
+  }
+  for (int l = 0; l < g->layers; ++l) {
+    g->xe.emplace_back(new Buf());
+    GK(g->xe.back()->ensure(E * XE * 2));
+    g->zm.emplace_back(new Buf());
+    GK(g->zm.back()->ensure(E * W * 4));
+    g->mm.emplace_back(new Buf());
+    GK(g->mm.back()->ensure(E * W * 4));
+    g->agg.emplace_back(new Buf());
+    GK(g->agg.back()->ensure(N * W * 4));
+    g->u.emplace_back(new Buf());
+    GK(g->u.back()->ensure(N * 2 * W * 2));
+    g->zu.emplace_back(new Buf());
+    GK(g->zu.back()->ensure(N * W * 4));
+    g->yu.emplace_back(new Buf());
+    GK(g->yu.back()->ensure(N * W * 4));
+  }
+  GK(g->o.ensure(N * g->OUTP * 4));
+  GK(g->dout.ensure(N * g->OUTP * 4));
+  GK(g->dh.ensure(N * W * 4));
+  GK(g->dh2.ensure(N * W * 4));
+  GK(g->dzu.ensure(N * W * 4));
+  GK(g->du.ensure(N * 2 * W * 4));
+  GK(g->dm.ensure(E * W * 4));
+  GK(g->dxe.ensure(E * XE * 4));
+  GK(g->t3.ensure(E * XE * 2 > N * g->OUTP * 2 ? E * XE * 2 : N * g->OUTP * 2));
+  g->capN = N;
+  return CELES_OK;
+}
+
+// graph and node features of RHS `rhs` of a context
+int prepare(celes_gnn* g, const CtxView& v, int rhs, double& scale) {
+  const int64_t N = v.N;
+  const int KN = g->knn;
+  int s = ensure_capacity(g, N);
+  if (s) return s;
+  if (KN == 16) knn_kernel<16><<<blocks(N, 128), 128, 0, g->stream>>>(static_cast<int>(N), static_cast<const Pos4*>(v.pos),
+                                                                       g->nbr.as<int>());
+  else return CELES_EINVAL;
+  note_launch();
+  GK(cudaGetLastError());
+  // reverse adjacency (host bookkeeping)
+  std::vector<int> nb(N * KN), off(N + 1, 0), re(N * KN);
+  GK(cudaMemcpyAsync(nb.data(), g->nbr.p, N * KN * 4, cudaMemcpyDeviceToHost, g->stream));
+  GK(cudaStreamSynchronize(g->stream));
+  for (int64_t e = 0; e < N * KN; ++e) off[nb[e] + 1]++;
+  for (int64_t i = 0; i < N; ++i) off[i + 1] += off[i];
+  std::vector<int> fill(off.begin(), off.end() - 1);
+  for (int64_t e = 0; e < N * KN; ++e) re[fill[nb[e]]++] = static_cast<int>(e);
+  GK(cudaMemcpyAsync(g->rev_off.p, off.data(), (N + 1) * 4, cudaMemcpyHostToDevice, g->stream));
+  GK(cudaMemcpyAsync(g->rev_edge.p, re.data(), N * KN * 4, cudaMemcpyHostToDevice, g->stream));
+  edge_features_kernel<<<blocks(N * KN), 256, 0, g->stream>>>(static_cast<int>(N), KN, static_cast<const Pos4*>(v.pos),
+                                                              g->nbr.as<int>(), v.k, g->ef.as<float>());
+  // scale: 1 / rms(T a)
+  const double* ta = v.rhs + (size_t)rhs * N * v.nmax * 2;
+  GK(g->lossd.ensure(16));
+  GK(cudaMemsetAsync(g->lossd.p, 0, 8, g->stream));
+  sumsq_kernel<<<256, 256, 0, g->stream>>>(N * v.nmax * 2, ta, g->lossd.as<double>());
+  double ss = 0.0;
+  GK(cudaMemcpyAsync(&ss, g->lossd.p, 8, cudaMemcpyDeviceToHost, g->stream));
+  GK(cudaStreamSynchronize(g->stream));
+  scale = ss > 0 ? 1.0 / std::sqrt(ss / (N * v.nmax * 2.0)) : 1.0;
+  node_features_kernel<<<blocks(N * g->F), 256, 0, g->stream>>>(static_cast<int>(N), v.nmax, g->F, ta, v.radii, v.nrel,
+                                                                 v.k, scale, g->feat.as<bf16>());
+  note_launch(4);
+  GK(cudaGetLastError());
+  return CELES_OK;
+}
+
+int forward(celes_gnn* g, int64_t N) {
+  const int W = g->width, KN = g->knn, XE = 2 * W + kEdgeFeat;
+  const int64_t E = N * KN;
+  const int n32 = static_cast<int>(N), e32 = static_cast<int>(E);
+  int s = gemm(g, n32, W, g->F, g->feat.p, g->F, g->in.w16.p, g->in.in, g->zin.as<float>(), W, 0.0f);
+  if (s) return s;
+  bias_relu_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N, W, g->zin.as<float>(), g->in.b.as<float>(),
+                                                        g->h[0]->as<float>(), nullptr, 1);
+  note_launch();
+  for (int l = 0; l < g->layers; ++l) {
+    Dense& dm = *g->msg[l];
+    Dense& du = *g->upd[l];
+    edge_input_kernel<<<blocks(E * XE), 256, 0, g->stream>>>(n32, KN, W, g->h[l]->as<float>(), g->nbr.as<int>(),
+                                                            g->ef.as<float>(), g->xe[l]->as<bf16>());
+    note_launch();
+    s = gemm(g, e32, W, XE, g->xe[l]->p, XE, dm.w16.p, dm.in, g->zm[l]->as<float>(), W, 0.0f);
+    if (s) return s;
+    bias_relu_kernel<<<blocks(E * W), 256, 0, g->stream>>>(E, W, g->zm[l]->as<float>(), dm.b.as<float>(),
+                                                          g->mm[l]->as<float>(), nullptr, 1);
+    aggregate_kernel<<<blocks(N * W), 256, 0, g->stream>>>(n32, KN, W, g->h[l]->as<float>(), g->mm[l]->as<float>(),
+                                                          g->agg[l]->as<float>(), g->u[l]->as<bf16>());
+    note_launch(2);
+    s = gemm(g, n32, W, 2 * W, g->u[l]->p, 2 * W, du.w16.p, du.in, g->zu[l]->as<float>(), W, 0.0f);
+    if (s) return s;
+    bias_relu_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N, W, g->zu[l]->as<float>(), du.b.as<float>(),
+                                                          g->yu[l]->as<float>(), nullptr, 1);
+    GK(cudaMemcpyAsync(g->h[l + 1]->p, g->h[l]->p, N * W * 4, cudaMemcpyDeviceToDevice, g->stream));
+    add_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N * W, g->h[l + 1]->as<float>(), g->yu[l]->as<float>());
+    note_launch(2);
+  }
+  to_bf16_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N * W, g->h[g->layers]->as<float>(), g->hin16.as<bf16>());
+  note_launch();
+  s = gemm(g, n32, g->OUTP, W, g->hin16.p, W, g->out.w16.p, g->out.in, g->o.as<float>(), g->OUTP, 0.0f);
+  if (s) return s;
+  bias_relu_kernel<<<blocks(N * g->OUTP), 256, 0, g->stream>>>(N, g->OUTP, g->o.as<float>(), g->out.b.as<float>(),
+                                                              nullptr, nullptr, 0);
+  note_launch();
+  GK(cudaGetLastError());
+  return CELES_OK;
+}
+
+int zero_grads(celes_gnn* g) {
+  auto z = [&](Dense& d) -> int {
+    GK(cudaMemsetAsync(d.g.p, 0, (size_t)d.out * d.in * 4, g->stream));
+    GK(cudaMemsetAsync(d.gb.p, 0, (size_t)d.out * 4, g->stream));
+    return CELES_OK;
+  };
+  int s = z(g->in) | z(g->out);
+  for (int l = 0; l < g->layers; ++l) s |= z(*g->msg[l]) | z(*g->upd[l]);
+  return s;
+}
+
+int backward(celes_gnn* g, int64_t N) {
+  const int W = g->width, KN = g->knn, XE = 2 * W + kEdgeFeat;
+  const int64_t E = N * KN;
+  const int n32 = static_cast<int>(N), e32 = static_cast<int>(E);
+  int s = zero_grads(g);
+  if (s) return s;
+  // output layer
+  s = dense_grad(g, g->out, n32, g->dout.as<float>(), g->hin16.as<bf16>());
+  if (s) return s;
+  to_bf16_kernel<<<blocks(N * g->OUTP), 256, 0, g->stream>>>(N * g->OUTP, g->dout.as<float>(), g->t3.as<bf16>());
+  note_launch();
+  s = gemm(g, n32, W, g->OUTP, g->t3.p, g->OUTP, g->out.wt16.p, g->out.out, g->dh.as<float>(), W, 0.0f);
+  if (s) return s;
+  for (int l = g->layers - 1; l >= 0; --l) {
+    Dense& dm = *g->msg[l];
+    Dense& du = *g->upd[l];
+    // update branch: dZu = dh * relu'(Zu)
+    GK(cudaMemcpyAsync(g->dzu.p, g->dh.p, N * W * 4, cudaMemcpyDeviceToDevice, g->stream));
+    relu_bwd_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N * W, g->zu[l]->as<float>(), g->dzu.as<float>());
+    note_launch();
+    s = dense_grad(g, du, n32, g->dzu.as<float>(), g->u[l]->as<bf16>());
+    if (s) return s;
+    to_bf16_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N * W, g->dzu.as<float>(), g->t3.as<bf16>());
+    note_launch();
+    s = gemm(g, n32, 2 * W, W, g->t3.p, W, du.wt16.p, du.out, g->du.as<float>(), 2 * W, 0.0f);
+    if (s) return s;
+    dh_from_update_kernel<<<blocks(N * W), 256, 0, g->stream>>>(n32, W, g->du.as<float>(), g->dh.as<float>());
+    // aggregation and messages
+    agg_bwd_kernel<<<blocks(E * W), 256, 0, g->stream>>>(n32, KN, W, g->du.as<float>(), g->dm.as<float>());
+    relu_bwd_kernel<<<blocks(E * W), 256, 0, g->stream>>>(E * W, g->zm[l]->as<float>(), g->dm.as<float>());
+    note_launch(3);
+    s = dense_grad(g, dm, e32, g->dm.as<float>(), g->xe[l]->as<bf16>());
+    if (s) return s;
+    to_bf16_kernel<<<blocks(E * W), 256, 0, g->stream>>>(E * W, g->dm.as<float>(), g->t3.as<bf16>());
+    note_launch();
+    s = gemm(g, e32, XE, W, g->t3.p, W, dm.wt16.p, dm.out, g->dxe.as<float>(), XE, 0.0f);
+    if (s) return s;
+    edge_scatter_kernel<<<blocks(N * W), 256, 0, g->stream>>>(n32, KN, W, g->dxe.as<float>(), g->rev_off.as<int>(),
+                                                             g->rev_edge.as<int>(), g->dh.as<float>());
+    note_launch();
+  }
+  // input layer: dZin = dh * relu'(Zin)
+  relu_bwd_kernel<<<blocks(N * W), 256, 0, g->stream>>>(N * W, g->zin.as<float>(), g->dh.as<float>());
+  note_launch();
+  s = dense_grad(g, g->in, n32, g->dh.as<float>(), g->feat.as<bf16>());
+  if (s) return s;
+  GK(cudaGetLastError());
+  return CELES_OK;
+}
+
+int adam(celes_gnn* g, float lr) {
+  ++g->step;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.0f - std::pow(b1, static_cast<float>(g->step));
+  const float c2 = 1.0f - std::pow(b2, static_cast<float>(g->step));
+  auto upd = [&](Dense& d) -> int {
+    const int64_t n = (int64_t)d.out * d.in;
+    adam_kernel<<<blocks(n), 256, 0, g->stream>>>(n, d.w.as<float>(), d.g.as<float>(), d.m1.as<float>(),
+                                                  d.m2.as<float>(), nullptr, lr, b1, b2, eps, c1, c2);
+    adam_kernel<<<blocks(d.out), 256, 0, g->stream>>>(d.out, d.b.as<float>(), d.gb.as<float>(), d.mb1.as<float>(),
+                                                      d.mb2.as<float>(), nullptr, lr, b1, b2, eps, c1, c2);
+    note_launch(2);
+    return dense_sync16(d, g->stream);
+  };
+  int s = upd(g->in) | upd(g->out);
+  for (int l = 0; l < g->layers; ++l) s |= upd(*g->msg[l]) | upd(*g->upd[l]);
+  return s;
+}
+
+int check_err(celes_gnn* g) {
+  int h = 0;
+  GK(cudaMemcpyAsync(&h, g->err.p, 4, cudaMemcpyDeviceToHost, g->stream));
+  GK(cudaStreamSynchronize(g->stream));
+  return h ? CELES_ETIMEOUT : CELES_OK;
+}
+
+}  // namespace
+
+extern "C" int celes_gnn_create(celes_gnn** out, int lmax, int width, int layers, int knn, uint64_t seed, int device) {
+  if (!out) return CELES_EINVAL;
+  *out = nullptr;
+  if (lmax < 1 || lmax > 5 || width < 16 || width > 512 || width % 16 || layers < 1 || layers > 8 || knn != 16)
+    return CELES_EINVAL;
+  std::unique_ptr<celes_gnn> g(new celes_gnn());
+  g->device = device;
+  g->lmax = lmax;
+  g->width = width;
+  g->layers = layers;
+  g->knn = knn;
+  g->nmax = 2 * lmax * (lmax + 2);
+  g->F = round8(2 * g->nmax + 3);
+  g->OUTP = round8(2 * g->nmax);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return CELES_ECUDA;
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return CELES_ECUDA;
+  std::mt19937_64 rng(seed);
+  int s = dense_init(g->in, width, g->F, rng, g->stream);
+  for (int l = 0; l < layers && !s; ++l) {
+    g->msg.emplace_back(new Dense());
+    s = dense_init(*g->msg.back(), width, 2 * width + kEdgeFeat, rng, g->stream);
+    g->upd.emplace_back(new Dense());
+    if (!s) s = dense_init(*g->upd.back(), width, 2 * width, rng, g->stream);
+  }
+  if (!s) s = dense_init(g->out, g->OUTP, width, rng, g->stream);
+  if (!s) {
+    // the output layer starts at zero: the untrained guess is T a
+    s = cudaMemsetAsync(g->out.w.p, 0, (size_t)g->out.out * g->out.in * 4, g->stream) != cudaSuccess ? CELES_ECUDA : 0;
+  }
+  if (!s) {
+    s = dense_sync16(g->in, g->stream) | dense_sync16(g->out, g->stream);
+    for (int l = 0; l < layers; ++l) s |= dense_sync16(*g->msg[l], g->stream) | dense_sync16(*g->upd[l], g->stream);
+  }
+  if (!s && g->err.ensure(4) != cudaSuccess) s = CELES_ENOMEM;
+  if (!s && cudaMemsetAsync(g->err.p, 0, 4, g->stream) != cudaSuccess) s = CELES_ECUDA;
+  if (!s && cudaStreamSynchronize(g->stream) != cudaSuccess) s = CELES_ECUDA;
+  cudaSetDevice(prev);
+  if (s) {
+    cudaStreamDestroy(g->stream);
+    return s;
+  }
+  *out = g.release();
+  return CELES_OK;
+}
+
+extern "C" void celes_gnn_destroy(celes_gnn* g) {
+  if (!g) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  if (g->stream) {
+    cudaStreamSynchronize(g->stream);
+    cudaStreamDestroy(g->stream);
+  }
+  delete g;
+  cudaSetDevice(prev);
+}
+
+extern "C" int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps, double lr, double* loss_out) {
+  if (!g || !ctx || steps < 0 || !(lr > 0.0)) return CELES_EINVAL;
+  CtxView v{};
+  int s = ctx_view(ctx, &v);
+  if (s) return s;
+  if (v.L != g->lmax || rhs < 0 || rhs >= v.nrhs) return CELES_EINVAL;
+  if (!v.has_b) return CELES_ESTATE;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  double scale = 1.0;
+  s = prepare(g, v, rhs, scale);
+  const int64_t N = v.N;
+  if (!s) {
+    const int64_t n = N * v.nmax * 2;
+    // target (b - T a) * scale, padded to OUTP columns
+    Buf tmp;
+    if (tmp.ensure(n * 4) != cudaSuccess) s = CELES_ENOMEM;
+    if (!s) {
+      target_kernel<<<blocks(n), 256, 0, g->stream>>>(n, v.b + (size_t)rhs * n, v.rhs + (size_t)rhs * n, scale,
+                                                       tmp.as<float>());
+      cudaMemsetAsync(g->tgt.p, 0, N * g->OUTP * 4, g->stream);
+      cudaMemcpy2DAsync(g->tgt.p, g->OUTP * 4, tmp.p, v.nmax * 2 * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
+                        g->stream);
+      note_launch();
+      double loss = 0.0;
+      // steps = 0: loss and gradients only (no update)
+      const int passes = steps > 0 ? steps : 1;
+      for (int it = 0; it < passes && !s; ++it) {
+        s = forward(g, N);
+        if (s) break;
+        cudaMemsetAsync(g->lossd.p, 0, 8, g->stream);
+        mse_kernel<<<256, 256, 0, g->stream>>>(N * g->OUTP, g->o.as<float>(), g->tgt.as<float>(),
+                                               g->dout.as<float>(), g->lossd.as<double>());
+        note_launch();
+        s = backward(g, N);
+        if (!s && steps > 0) s = adam(g, static_cast<float>(lr));
+        if (!s && it == passes - 1) {
+          cudaMemcpyAsync(&loss, g->lossd.p, 8, cudaMemcpyDeviceToHost, g->stream);
+        }
+      }
+      if (!s) s = check_err(g);
+      if (!s && loss_out) *loss_out = loss;
+    }
+  }
+  cudaSetDevice(prev);
+  return s;
+}
+
+extern "C" int celes_gnn_predict(celes_gnn* g, celes_ctx* ctx) {
+  if (!g || !ctx) return CELES_EINVAL;
+  CtxView v{};
+  int s = ctx_view(ctx, &v);
+  if (s) return s;
+  if (v.L != g->lmax || v.nrhs < 1) return CELES_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  const int64_t N = v.N;
+  const int64_t n = N * v.nmax * 2;
+  Buf o2, b0;
+  if (o2.ensure(n * 4) != cudaSuccess || b0.ensure(n * 8) != cudaSuccess) s = CELES_ENOMEM;
+  for (int r = 0; r < v.nrhs && !s; ++r) {
+    double scale = 1.0;
+    s = prepare(g, v, r, scale);
+    if (!s) s = forward(g, N);
+    if (!s) {
+      cudaMemcpy2DAsync(o2.p, v.nmax * 2 * 4, g->o.p, g->OUTP * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
+                        g->stream);
+      guess_kernel<<<blocks(n), 256, 0, g->stream>>>(n, v.rhs + (size_t)r * n, o2.as<float>(), 1.0 / scale,
+                                                     b0.as<double>());
+      note_launch();
+      s = check_err(g);
+      if (!s) s = ctx_set_learned_guess(ctx, r, b0.as<double>());
+    }
+  }
+  cudaSetDevice(prev);
+  return s;
+}
+
+extern "C" int celes_gnn_num_params(const celes_gnn* g) {
+  if (!g) return CELES_EINVAL;
+  auto c = [](const Dense& d) { return d.out * d.in + d.out; };
+  int n = c(g->in) + c(g->out);
+  for (int l = 0; l < g->layers; ++l) n += c(*g->msg[l]) + c(*g->upd[l]);
+  return n;
+}
+
+// parameters (what = 0) or their gradients (what = 1) as FP32, layer by layer
+// (input, then message and update of each round, then output), each as the
+// weight [out][in] row-major followed by the bias [out]
+extern "C" int celes_gnn_export(celes_gnn* g, int what, float* host, int cap) {
+  if (!g || (what != 0 && what != 1)) return CELES_EINVAL;
+  std::vector<Dense*> ds{&g->in};
+  for (int l = 0; l < g->layers; ++l) {
+    ds.push_back(g->msg[l].get());
+    ds.push_back(g->upd[l].get());
+  }
+  ds.push_back(&g->out);
+  int total = 0;
+  for (Dense* d : ds) total += d->out * d->in + d->out;
+  if (!host) return total;
+  if (cap < total) return CELES_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  size_t off = 0;
+  for (Dense* d : ds) {
+    const size_t nw = (size_t)d->out * d->in;
+    const void* w = what == 0 ? d->w.p : d->g.p;
+    const void* b = what == 0 ? d->b.p : d->gb.p;
+    if (cudaMemcpyAsync(host + off, w, nw * 4, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(host + off + nw, b, d->out * 4, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess) {
+      cudaSetDevice(prev);
+      return CELES_ECUDA;
+    }
+    off += nw + d->out;
+  }
+  const cudaError_t e = cudaStreamSynchronize(g->stream);
+  cudaSetDevice(prev);
+  return e == cudaSuccess ? total : CELES_ECUDA;
+}

@@ -271,37 +271,49 @@ cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, do
 // ---------------------------------------------------------------------------
 constexpr int kVecThreads = 256;
 
-// partial[b][j] = sum over this block's range of conj(V_j) w   (FP64 accumulation)
+// partial[b][j] = sum over this block's range of conj(V_j) w, eight vectors per
+// pass (w read once per pass); per-thread and warp sums in the vector's own
+// precision (a handful of terms each), block sums in FP64
 template <typename R>
 __global__ void multi_dotc_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V, int64_t ldv,
                                   const Pair2<R>* __restrict__ w, double* __restrict__ partial) {
-  __shared__ double red[2][kVecThreads / 32];
+  constexpr int JT = 8;
+  __shared__ double red[2 * JT][kVecThreads / 32];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < nv; ++j) {
-    double sr = 0.0, si = 0.0;
-    const Pair2<R>* v = V + j * ldv;
+  for (int j0 = 0; j0 < nv; j0 += JT) {
+    const int nj = nv - j0 < JT ? nv - j0 : JT;
+    R sr[JT], si[JT];
+#pragma unroll
+    for (int q = 0; q < JT; ++q) sr[q] = si[q] = static_cast<R>(0);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
-      const Pair2<R> a = v[t], b = w[t];
-      sr += static_cast<double>(a.re) * b.re + static_cast<double>(a.im) * b.im;
-      si += static_cast<double>(a.re) * b.im - static_cast<double>(a.im) * b.re;
+      const Pair2<R> b = w[t];
+#pragma unroll
+      for (int q = 0; q < JT; ++q) {
+        if (q < nj) {
+          const Pair2<R> a = V[(j0 + q) * ldv + t];
+          sr[q] = fma_(a.re, b.re, fma_(a.im, b.im, sr[q]));
+          si[q] = fma_(a.re, b.im, fma_(-a.im, b.re, si[q]));
+        }
+      }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_down_sync(0xffffffffu, sr, o);
-      si += __shfl_down_sync(0xffffffffu, si, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = sr;
-      red[1][threadIdx.x >> 5] = si;
+#pragma unroll
+    for (int q = 0; q < JT; ++q) {
+      R a = sr[q], b = si[q];
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        red[2 * q][threadIdx.x >> 5] = static_cast<double>(a);
+        red[2 * q + 1][threadIdx.x >> 5] = static_cast<double>(b);
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int q = 0; q < kVecThreads / 32; ++q) {
-        a += red[0][q];
-        b += red[1][q];
-      }
-      partial[((int64_t)blockIdx.x * nv + j) * 2] = a;
-      partial[((int64_t)blockIdx.x * nv + j) * 2 + 1] = b;
+    if (threadIdx.x < 2 * nj) {
+      double s = 0.0;
+      for (int q = 0; q < kVecThreads / 32; ++q) s += red[threadIdx.x][q];
+      const int q = threadIdx.x >> 1;
+      partial[((int64_t)blockIdx.x * nv + j0 + q) * 2 + (threadIdx.x & 1)] = s;
     }
     __syncthreads();
   }
@@ -356,19 +368,24 @@ template cudaError_t launch_multi_dotc<float>(int64_t, int, const void*, int64_t
 template cudaError_t launch_multi_dotc<double>(int64_t, int, const void*, int64_t, const void*, double*, double*,
                                                cudaStream_t);
 
-// w <- alpha0 * w - sum_j h_j V_j   (h given as FP64 complex on the device)
+// w <- alpha0 * w - sum_j h_j V_j   (h given as FP64 complex on the device;
+// arithmetic in the vector's precision)
 template <typename R>
 __global__ void multi_axpy_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V, int64_t ldv,
                                   const double* __restrict__ h, double alpha0, Pair2<R>* __restrict__ w) {
+  __shared__ R hs[2 * 128];
+  for (int q = threadIdx.x; q < 2 * nv && q < 256; q += blockDim.x) hs[q] = static_cast<R>(h[q]);
+  __syncthreads();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    double ar = alpha0 * w[t].re, ai = alpha0 * w[t].im;
+    R ar = static_cast<R>(alpha0) * w[t].re, ai = static_cast<R>(alpha0) * w[t].im;
     for (int j = 0; j < nv; ++j) {
       const Pair2<R> v = V[j * ldv + t];
-      const double hr = h[2 * j], hi = h[2 * j + 1];
-      ar -= hr * v.re - hi * v.im;
-      ai -= hr * v.im + hi * v.re;
+      const R hr = j < 128 ? hs[2 * j] : static_cast<R>(h[2 * j]);
+      const R hi = j < 128 ? hs[2 * j + 1] : static_cast<R>(h[2 * j + 1]);
+      ar = fma_(-hr, v.re, fma_(hi, v.im, ar));
+      ai = fma_(-hr, v.im, fma_(-hi, v.re, ai));
     }
-    w[t] = Pair2<R>{static_cast<R>(ar), static_cast<R>(ai)};
+    w[t] = Pair2<R>{ar, ai};
   }
 }
 
@@ -377,18 +394,18 @@ template <typename R>
 __global__ void multi_combine_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V, int64_t ldv,
                                      const double* __restrict__ c, double beta, Pair2<R>* __restrict__ y) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    double ar = 0.0, ai = 0.0;
+    R ar = 0, ai = 0;
     if (beta != 0.0) {
-      ar = beta * y[t].re;
-      ai = beta * y[t].im;
+      ar = static_cast<R>(beta) * y[t].re;
+      ai = static_cast<R>(beta) * y[t].im;
     }
     for (int j = 0; j < nv; ++j) {
       const Pair2<R> v = V[j * ldv + t];
-      const double cr = c[2 * j], ci = c[2 * j + 1];
-      ar += cr * v.re - ci * v.im;
-      ai += cr * v.im + ci * v.re;
+      const R cr = static_cast<R>(c[2 * j]), ci = static_cast<R>(c[2 * j + 1]);
+      ar = fma_(cr, v.re, fma_(-ci, v.im, ar));
+      ai = fma_(cr, v.im, fma_(ci, v.re, ai));
     }
-    y[t] = Pair2<R>{static_cast<R>(ar), static_cast<R>(ai)};
+    y[t] = Pair2<R>{ar, ai};
   }
 }
 

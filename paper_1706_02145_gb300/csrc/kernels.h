@@ -5,7 +5,25 @@
 
 #include <cstdint>
 
+struct celes_ctx;
+
 namespace celes {
+
+// read-only view of a context's device data (for the learned-guess module)
+struct CtxView {
+  int64_t N;
+  int L, nmax, nrhs;
+  double k;
+  const void* pos;       // [N] Pos4
+  const double* radii;   // [N]
+  const double* nrel;    // [N] complex
+  const double* rhs;     // [nrhs][N][nmax] complex, T a_in
+  const double* b;       // [nrhs][N][nmax] complex, current solution
+  bool has_b;
+};
+int ctx_view(celes_ctx* c, CtxView* v);
+// store a learned first iterate for RHS `rhs` (device pointer, complex128 [N][nmax])
+int ctx_set_learned_guess(celes_ctx* c, int rhs, const double* b0_dev);
 
 // process-wide count of kernels launched by this library
 void note_launch(int n = 1);
@@ -51,6 +69,10 @@ cudaError_t launch_nonfinite(int64_t n, const void* v, int* flag, cudaStream_t s
 cudaError_t launch_farfield(int64_t N, int L, double k, const void* pos, const double* b, int64_t Nd,
                             const double* dirs, double* g, cudaStream_t st);
 cudaError_t launch_overlap_check(int64_t N, const void* pos, const double* radii, int* flag, cudaStream_t st);
+
+// tensor-core GEMM (tc_gemm.cu): C = alpha A B^T + beta C, BF16 in, FP32 out
+cudaError_t launch_gemm_bf16_tn(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                                float alpha, float beta, int* err, cudaStream_t st);
 
 // block-diagonal preconditioner (precond.cu)
 cudaError_t launch_precond_assemble(int L, int64_t nblocks, const int64_t* block_off, const int64_t* mat_off,

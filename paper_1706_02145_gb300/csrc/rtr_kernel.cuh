@@ -21,6 +21,11 @@
 namespace celes {
 namespace rtr {
 
+template <typename R>
+struct alignas(4 * sizeof(R)) Quad4 {
+  R x, y, z, w;
+};
+
 template <int L, typename R>
 struct Geom {
   R hre[2 * L + 1], him[2 * L + 1];
@@ -28,63 +33,169 @@ struct Geom {
   R ere[L + 1], eim[L + 1];
 };
 
+// ---- FP32 pair geometry without FP64 arithmetic ----------------------------
+// Positions are scaled by k and split into float pairs (hi + lo, 48
+// significant bits).  Per pair, k|d| is formed with error-free float
+// transformations (two-sum and fma-based two-product, Knuth / Dekker) to about
+// 2^-44 relative, then reduced mod pi/2 with an exact fma (the product of an
+// integer quadrant count and the float nearest pi/2 has no bits below 2^-23),
+// so the phase e^{i k|d|} keeps FP32 accuracy at any cluster size while the
+// FP64 pipe (1/64 of the FP32 rate on this part) stays idle.
+struct alignas(16) PosFF {
+  float xh, yh, zh, ph;
+  float xl, yl, zl, pl;
+};
+
+static_assert(sizeof(PosFF) == sizeof(Pos4), "the source tile holds either form");
+
+__device__ __forceinline__ PosFF split_pos(const Pos4& p, double k) {
+  const double x = k * p.x, y = k * p.y, z = k * p.z;
+  PosFF o;
+  o.xh = static_cast<float>(x);
+  o.yh = static_cast<float>(y);
+  o.zh = static_cast<float>(z);
+  o.xl = static_cast<float>(x - static_cast<double>(o.xh));
+  o.yl = static_cast<float>(y - static_cast<double>(o.yh));
+  o.zl = static_cast<float>(z - static_cast<double>(o.zh));
+  o.ph = o.pl = 0.0f;
+  return o;
+}
+
+// s + e == a - b exactly (two-sum of a and -b)
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
+  s = __fsub_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
+}
+// s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// sin and cos of q pi/2 + y, |y| <= pi/4 (+ rounding): Taylor series to y^9 /
+// y^10 (truncation below 2e-9), quadrant q mod 4 selects signs and the swap
+__device__ __forceinline__ void sincos_quadrant(float y, int iq, float& s, float& c) {
+  const float y2 = y * y;
+  float ps = fma_(y2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fma_(y2, ps, 1.0f / 120.0f);
+  ps = fma_(y2, ps, -1.0f / 6.0f);
+  const float sr = fma_(y * y2, ps, y);
+  float pc = fma_(y2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fma_(y2, pc, -1.0f / 720.0f);
+  pc = fma_(y2, pc, 1.0f / 24.0f);
+  pc = fma_(y2, pc, -0.5f);
+  const float cr = fma_(y2, pc, 1.0f);
+  const float s0 = (iq & 1) ? cr : sr;
+  const float c0 = (iq & 1) ? sr : cr;
+  s = (iq & 2) ? -s0 : s0;
+  c = ((iq + 1) & 2) ? -c0 : c0;
+}
+
+template <int L, typename R>
+__device__ __forceinline__ void geometry_angles_t(R ct, R st, R cph, R sph, Geom<L, R>& g);
+template <int L>
+__device__ __forceinline__ void geometry_angles(float ct, float st, float cph, float sph, Geom<L, float>& g) {
+  geometry_angles_t<L, float>(ct, st, cph, sph, g);
+}
+
+template <int L>
+__device__ __forceinline__ void geometry_ff(const PosFF& a, const PosFF& b, Geom<L, float>& g) {
+  constexpr int PM = 2 * L;
+  // k (r_a - r_b) per axis as s + e (unnormalised; |e| << |s| or s == 0)
+  float sx, ex, sy, ey, sz, ez;
+  two_diff(a.xh, b.xh, sx, ex);
+  two_diff(a.yh, b.yh, sy, ey);
+  two_diff(a.zh, b.zh, sz, ez);
+  ex = __fadd_rn(ex, __fsub_rn(a.xl, b.xl));
+  ey = __fadd_rn(ey, __fsub_rn(a.yl, b.yl));
+  ez = __fadd_rn(ez, __fsub_rn(a.zl, b.zl));
+  // (k d)^2 = sum (s + e)^2 = sum s^2 (exact two-products) + e (2 s + e)
+  const float px = __fmul_rn(sx, sx), py = __fmul_rn(sy, sy), pz = __fmul_rn(sz, sz);
+  float lo = __fadd_rn(__fadd_rn(__fmaf_rn(sx, sx, -px), __fmaf_rn(sy, sy, -py)), __fmaf_rn(sz, sz, -pz));
+  lo = __fmaf_rn(ex, __fmaf_rn(2.0f, sx, ex), lo);
+  lo = __fmaf_rn(ey, __fmaf_rn(2.0f, sy, ey), lo);
+  lo = __fmaf_rn(ez, __fmaf_rn(2.0f, sz, ez), lo);
+  float S, E1, S2, E2;
+  two_sum(px, py, S, E1);
+  two_sum(S, pz, S2, E2);
+  lo = __fadd_rn(lo, __fadd_rn(E1, E2));
+  // k d = r + delta: one Newton correction of the FP32 square root
+  const float rinv = rsqrtf(S2);
+  const float r = __fmul_rn(S2, rinv);
+  const float rr = __fmul_rn(r, r);
+  const float rre = __fmaf_rn(r, r, -rr);
+  const float resid = __fadd_rn(__fsub_rn(__fsub_rn(S2, rr), rre), lo);
+  const float delta = __fmul_rn(resid, 0.5f * rinv);
+  // phase: k d = n pi/2 + y
+  constexpr double HALF_PI = 1.5707963267948966192313216916398;
+  constexpr float H1 = static_cast<float>(HALF_PI);
+  constexpr float H2 = static_cast<float>(HALF_PI - static_cast<double>(H1));
+  const float n = rintf(__fmul_rn(r, static_cast<float>(1.0 / HALF_PI)));
+  float y = __fmaf_rn(-n, H1, r);  // exact
+  y = __fadd_rn(y, __fmaf_rn(-n, H2, delta));
+  float sn, cs;
+  sincos_quadrant(y, static_cast<int>(n) & 3, sn, cs);
+  const float kd = __fadd_rn(r, delta);
+  const float ix = 1.0f / kd;
+  g.hre[0] = sn * ix;
+  g.him[0] = -cs * ix;
+  g.hre[1] = -ix * fma_(-sn, ix, cs);
+  g.him[1] = -ix * fma_(cs, ix, sn);
+#pragma unroll
+  for (int p = 1; p < PM; ++p) {
+    const float c = static_cast<float>(2 * p + 1) * ix;
+    g.hre[p + 1] = fma_(c, g.hre[p], -g.hre[p - 1]);
+    g.him[p + 1] = fma_(c, g.him[p], -g.him[p - 1]);
+  }
+  const float dxf = __fadd_rn(sx, ex), dyf = __fadd_rn(sy, ey), dzf = __fadd_rn(sz, ez);
+  const float rho = sqrtf(fma_(dxf, dxf, dyf * dyf));
+  const float ct = fminf(1.0f, fmaxf(-1.0f, dzf * rinv));
+  const float st = fminf(1.0f, rho * rinv);
+  const float ir = rho > 0.0f ? 1.0f / rho : 0.0f;
+  const float cph = rho > 0.0f ? dxf * ir : 1.0f;
+  const float sph = dyf * ir;
+  geometry_angles<L>(ct, st, cph, sph, g);
+}
+
+// FP64 pair geometry (the FP64 kernel)
 template <int L, typename R>
 __device__ __forceinline__ void geometry(double dx, double dy, double dz, double k, Geom<L, R>& g) {
+  static_assert(sizeof(R) == 8, "the FP32 kernel uses geometry_ff");
   constexpr int PM = 2 * L;
   const double d2 = fma_(dx, dx, fma_(dy, dy, dz * dz));
-  R ct, st, cph, sph;
-  if constexpr (sizeof(R) == 4) {
-    const float rinv = rsqrtf(static_cast<float>(d2));
-    double d = d2 * static_cast<double>(rinv);
-    d = fma_(0.5 * static_cast<double>(rinv), fma_(-d, d, d2), d);
-    const double kd = k * d;
-    float sn, cs;
-    sincos_kd(kd, sn, cs);
-    const float ix = 1.0f / static_cast<float>(kd);
-    g.hre[0] = sn * ix;
-    g.him[0] = -cs * ix;
-    g.hre[1] = -ix * fma_(-sn, ix, cs);
-    g.him[1] = -ix * fma_(cs, ix, sn);
+  const double d = sqrt(d2);
+  const double kd = k * d;
+  const double TWO_PI = 6.283185307179586476925286766559;
+  const double ph = fma_(-rint(kd * (1.0 / TWO_PI)), TWO_PI, kd);
+  double sn, cs;
+  sincos(ph, &sn, &cs);
+  const double ix = 1.0 / kd;
+  g.hre[0] = sn * ix;
+  g.him[0] = -cs * ix;
+  g.hre[1] = -ix * fma_(-sn, ix, cs);
+  g.him[1] = -ix * fma_(cs, ix, sn);
 #pragma unroll
-    for (int p = 1; p < PM; ++p) {
-      const float a = static_cast<float>(2 * p + 1) * ix;
-      g.hre[p + 1] = fma_(a, g.hre[p], -g.hre[p - 1]);
-      g.him[p + 1] = fma_(a, g.him[p], -g.him[p - 1]);
-    }
-    const float id = static_cast<float>(1.0 / d);
-    const float dxf = static_cast<float>(dx), dyf = static_cast<float>(dy), dzf = static_cast<float>(dz);
-    const float rho = sqrtf(fma_(dxf, dxf, dyf * dyf));
-    ct = dzf * id;
-    st = rho * id;
-    const float ir = rho > 0.0f ? 1.0f / rho : 0.0f;
-    cph = rho > 0.0f ? dxf * ir : 1.0f;
-    sph = dyf * ir;
-  } else {
-    const double d = sqrt(d2);
-    const double kd = k * d;
-    const double TWO_PI = 6.283185307179586476925286766559;
-    const double ph = fma_(-rint(kd * (1.0 / TWO_PI)), TWO_PI, kd);
-    double sn, cs;
-    sincos(ph, &sn, &cs);
-    const double ix = 1.0 / kd;
-    g.hre[0] = sn * ix;
-    g.him[0] = -cs * ix;
-    g.hre[1] = -ix * fma_(-sn, ix, cs);
-    g.him[1] = -ix * fma_(cs, ix, sn);
-#pragma unroll
-    for (int p = 1; p < PM; ++p) {
-      const double a = static_cast<double>(2 * p + 1) * ix;
-      g.hre[p + 1] = fma_(a, g.hre[p], -g.hre[p - 1]);
-      g.him[p + 1] = fma_(a, g.him[p], -g.him[p - 1]);
-    }
-    const double id = 1.0 / d;
-    const double rho = sqrt(fma_(dx, dx, dy * dy));
-    ct = dz * id;
-    st = rho * id;
-    const double ir = rho > 0.0 ? 1.0 / rho : 0.0;
-    cph = rho > 0.0 ? dx * ir : 1.0;
-    sph = dy * ir;
+  for (int p = 1; p < PM; ++p) {
+    const double a = static_cast<double>(2 * p + 1) * ix;
+    g.hre[p + 1] = fma_(a, g.hre[p], -g.hre[p - 1]);
+    g.him[p + 1] = fma_(a, g.him[p], -g.him[p - 1]);
   }
+  const double id = 1.0 / d;
+  const double rho = sqrt(fma_(dx, dx, dy * dy));
+  const double ct = dz * id;
+  const double st = rho * id;
+  const double ir = rho > 0.0 ? 1.0 / rho : 0.0;
+  const double cph = rho > 0.0 ? dx * ir : 1.0;
+  const double sph = dy * ir;
+  geometry_angles_t<L, R>(ct, st, cph, sph, g);
+}
+
+// half angles, their powers and e^{i m phi}
+template <int L, typename R>
+__device__ __forceinline__ void geometry_angles_t(R ct, R st, R cph, R sph, Geom<L, R>& g) {
+  constexpr int PM = 2 * L;
   // half angles without cancellation: c = sqrt((1+ct)/2), s = st/(2c) for
   // ct >= 0, and the mirror formulas otherwise
   R c, s;
@@ -299,14 +410,15 @@ __device__ __forceinline__ void rot_bwd_col(const Geom<L, R>& g, const R* dv, YV
   const R er = g.ere[AM];
   const R ei = M < 0 ? g.eim[AM] : -g.eim[AM];  // e^{-i M phi}
   constexpr int r = Row<l, M>::r;
-  R& c0 = acc(2 * r);
-  R& c1 = acc(2 * r + 1);
-  c0 = fma_(a0, er, fma_(-a1, ei, c0));
-  c1 = fma_(a0, ei, fma_(a1, er, c1));
-  R& d0 = acc(2 * (NH + r));
-  R& d1 = acc(2 * (NH + r) + 1);
-  d0 = fma_(b0, er, fma_(-b1, ei, d0));
-  d1 = fma_(b0, ei, fma_(b1, er, d1));
+  // row r of the receiver's sums: (y+ re, y+ im, y- re, y- im)
+  R c[4];
+  acc.load(r, c);
+  c[0] = fma_(a0, er, fma_(-a1, ei, c[0]));
+  c[1] = fma_(a0, ei, fma_(a1, er, c[1]));
+  c[2] = fma_(b0, er, fma_(-b1, ei, c[2]));
+  c[3] = fma_(b0, ei, fma_(b1, er, c[3]));
+  acc.store(r, c);
+  (void)NH;
 }
 
 template <int L, int l, typename R, typename YV, typename Acc, int... MI>
@@ -333,6 +445,38 @@ template <typename R, int BLOCK>
 struct AccSmem {
   R* a;
   __device__ __forceinline__ R& operator()(int q) const { return a[q * BLOCK]; }
+};
+
+// receiver sums, one 4-vector (y+ re, y+ im, y- re, y- im) per output row:
+// registers [NH][4], or shared memory [NH][BLOCK] of 4-vectors (one 16- or
+// 32-byte access per row)
+template <typename R>
+struct RowAccReg {
+  R* a;
+  __device__ __forceinline__ void load(int r, R (&c)[4]) const {
+    c[0] = a[4 * r];
+    c[1] = a[4 * r + 1];
+    c[2] = a[4 * r + 2];
+    c[3] = a[4 * r + 3];
+  }
+  __device__ __forceinline__ void store(int r, const R (&c)[4]) const {
+    a[4 * r] = c[0];
+    a[4 * r + 1] = c[1];
+    a[4 * r + 2] = c[2];
+    a[4 * r + 3] = c[3];
+  }
+};
+template <typename R, int BLOCK>
+struct RowAccSmem {
+  Quad4<R>* a;  // this thread's element of row 0
+  __device__ __forceinline__ void load(int r, R (&c)[4]) const {
+    const Quad4<R> v = a[r * BLOCK];
+    c[0] = v.x;
+    c[1] = v.y;
+    c[2] = v.z;
+    c[3] = v.w;
+  }
+  __device__ __forceinline__ void store(int r, const R (&c)[4]) const { a[r * BLOCK] = Quad4<R>{c[0], c[1], c[2], c[3]}; }
 };
 
 template <int L, typename R, typename XV, typename YV, typename Acc>
@@ -385,12 +529,16 @@ __global__ void __launch_bounds__(Config<L, R>::BLOCK)
   const int j0 = blockIdx.y * chunk;
   const int j1 = min(N, j0 + chunk);
   const bool active = i < N;
+  constexpr bool FF = sizeof(R) == 4;  // FP32: float-float positions scaled by k
   Pos4 ri = Pos4{0, 0, 0, 0};
   if (active) ri = pos[i];
+  const PosFF rf = split_pos(ri, k);
+  PosFF* sposf = reinterpret_cast<PosFF*>(spos);
 
   R areg[C::ACC_SMEM ? 1 : 4 * NH];
+  Quad4<R>* sacc4 = reinterpret_cast<Quad4<R>*>(sacc);
   if constexpr (C::ACC_SMEM) {
-    for (int q = 0; q < 4 * NH; ++q) sacc[q * BLOCK + tid] = static_cast<R>(0);
+    for (int r = 0; r < NH; ++r) sacc4[r * BLOCK + tid] = Quad4<R>{0, 0, 0, 0};
   } else {
 #pragma unroll
     for (int q = 0; q < 4 * NH; ++q) areg[q] = static_cast<R>(0);
@@ -407,21 +555,29 @@ __global__ void __launch_bounds__(Config<L, R>::BLOCK)
       sx[jj * 2 * NH + r] = Pair2<R>{a.re + b.re, a.im + b.im};
       sx[jj * 2 * NH + NH + r] = Pair2<R>{a.re - b.re, a.im - b.im};
     }
-    for (int q = tid; q < nj; q += BLOCK) spos[q] = pos[jt + q];
+    if constexpr (FF) {
+      for (int q = tid; q < nj; q += BLOCK) sposf[q] = split_pos(pos[jt + q], k);
+    } else {
+      for (int q = tid; q < nj; q += BLOCK) spos[q] = pos[jt + q];
+    }
     __syncthreads();
     if (active) {
       for (int jj = 0; jj < nj; ++jj) {
         if (jt + jj == i) continue;  // no self coupling
-        const Pos4 rj = spos[jj];
         Geom<L, R> g;
-        geometry<L, R>(ri.x - rj.x, ri.y - rj.y, ri.z - rj.z, k, g);
+        if constexpr (FF) {
+          geometry_ff<L>(rf, sposf[jj], g);
+        } else {
+          const Pos4 rj = spos[jj];
+          geometry<L, R>(ri.x - rj.x, ri.y - rj.y, ri.z - rj.z, k, g);
+        }
         const Pair2<R>* xs = sx + jj * 2 * NH;
         auto run = [&](auto& xp, auto& yp) {
           if constexpr (C::ACC_SMEM) {
-            AccSmem<R, BLOCK> acc{sacc + tid};
+            RowAccSmem<R, BLOCK> acc{sacc4 + tid};
             pair<L, R>(g, xs, xp, yp, acc);
           } else {
-            AccReg<R> acc{areg};
+            RowAccReg<R> acc{areg};
             pair<L, R>(g, xs, xp, yp, acc);
           }
         };
@@ -439,12 +595,20 @@ __global__ void __launch_bounds__(Config<L, R>::BLOCK)
     }
   }
   if (active) {
-    R* out = reinterpret_cast<R*>(partial + ((size_t)blockIdx.y * N + i) * (2 * NH));
+    // partial layout [2][NH] complex: y+ rows, then y- rows
+    Pair2<R>* out = partial + ((size_t)blockIdx.y * N + i) * (2 * NH);
     if constexpr (C::ACC_SMEM) {
-      for (int q = 0; q < 4 * NH; ++q) out[q] = sacc[q * BLOCK + tid];
+      for (int r = 0; r < NH; ++r) {
+        const Quad4<R> v = sacc4[r * BLOCK + tid];
+        out[r] = Pair2<R>{v.x, v.y};
+        out[NH + r] = Pair2<R>{v.z, v.w};
+      }
     } else {
 #pragma unroll
-      for (int q = 0; q < 4 * NH; ++q) out[q] = areg[q];
+      for (int r = 0; r < NH; ++r) {
+        out[r] = Pair2<R>{areg[4 * r], areg[4 * r + 1]};
+        out[NH + r] = Pair2<R>{areg[4 * r + 2], areg[4 * r + 3]};
+      }
     }
   }
 }
