@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-rows", type=int, default=0, help="receivers in the CPU sample (0 = auto)")
     ap.add_argument("--small-n", type=int, default=2000, help="spheres of the measured plain-FP64 comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-ensemble measurement")
+    ap.add_argument("--batched-ensembles", type=int, default=12)
+    ap.add_argument("--batched-rhs", type=int, default=4)
     return ap.parse_args()
 
 
@@ -212,6 +215,62 @@ def run_reference(args, rank):
 # our arm
 # ---------------------------------------------------------------------------
 
+def run_batched(args, local_rank):
+    """Many uneven ensembles x RHS in one lockstep batched solve against the
+    same systems solved one context at a time (ensembles of the multi-ensemble
+    recipe: lmax 2..5, plane waves from a 60 degree cap; sizes scaled by 0.4
+    so the measurement takes seconds)."""
+    import torch
+    import synth
+    from paper_1706_02145_gb300 import binding as B
+    scenes = []
+    for e in range(args.batched_ensembles):
+        full = synth.config3(e, n_rhs=args.batched_rhs)
+        scenes.append(synth.config3(e, n_rhs=args.batched_rhs, N=max(80, int(0.4 * full.N))))
+    ctxs = []
+    try:
+        for sc in scenes:
+            c = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, device=local_rank)
+            ctxs.append(c)
+            B.celes_set_incident(c, [B.make_incident("plane", beta=i.beta, alpha=i.alpha, pol=i.pol)
+                                     for i in sc.incidents])
+        bt = B.celes_batch_create(ctxs, restart=30)
+        try:
+            n = B.celes_batch_num_unknowns(bt)
+            x = torch.ones(n, dtype=torch.complex64, device=f"cuda:{local_rank}")
+            y = torch.empty_like(x)
+            B.celes_batch_master_matvec(bt, x, y, precision=B.CELES_FP32)  # graph capture, warm-up
+            reps = 5
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                B.celes_batch_master_matvec(bt, x, y, precision=B.CELES_FP32)
+            t_mv = (time.perf_counter() - t0) / reps
+            pairs = sum(sc.N * (sc.N - 1) * len(sc.incidents) for sc in scenes)
+            code, infos = B.celes_batch_solve(bt, len(ctxs), TOL, mode=B.CELES_SOLVE_MIXED, restart=30,
+                                              raise_on_noconv=False)
+            t_batch = max(i["seconds"] for i in infos)
+            res_batch = max(i["residual"] for i in infos)
+            its_batch = max(i["iterations"] for i in infos)
+        finally:
+            B.celes_batch_destroy(bt)
+        t_one, res_one = 0.0, 0.0
+        for c in ctxs:
+            info = B.celes_solve(c, TOL, mode=B.CELES_SOLVE_MIXED, restart=30, use_precond=False,
+                                 raise_on_noconv=False)
+            t_one += info["seconds"]
+            res_one = max(res_one, info["residual"])
+        return {"ensembles": len(scenes), "rhs_each": args.batched_rhs, "systems": len(scenes) * args.batched_rhs,
+                "N_range": [min(sc.N for sc in scenes), max(sc.N for sc in scenes)],
+                "lmax_values": sorted({sc.lmax for sc in scenes}),
+                "operator_fp32_ms": t_mv * 1e3, "operator_couplings_per_s": pairs / t_mv,
+                "batched_solve_s": t_batch, "batched_max_iterations": its_batch, "batched_max_residual": res_batch,
+                "one_by_one_solve_s": t_one, "one_by_one_max_residual": res_one, "speedup": t_one / t_batch,
+                "note": "mixed FP32/FP64 GMRES(30) to 1e-6, no preconditioner, first iterate T a, both forms"}
+    finally:
+        for c in ctxs:
+            B.celes_destroy(c)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import synth
@@ -333,14 +392,23 @@ def run_ours(args, rank, world, local_rank):
             bm = B.celes_get_coefficients(cs)[0]
             ip = B.celes_solve(cs, TOL, mode=B.CELES_SOLVE_FP64, raise_on_noconv=False)
             bp = B.celes_get_coefficients(cs)[0]
+            ib = B.celes_solve(cs, TOL, mode=B.CELES_SOLVE_MIXED, solver=B.CELES_SOLVER_BICGSTAB,
+                               raise_on_noconv=False)
+            bb = B.celes_get_coefficients(cs)[0]
             tt["measured_small"] = {"N": small.N, "chosen_s": im["seconds"], "chosen_iterations": im["iterations"],
                                     "plain_fp64_s": ip["seconds"], "plain_fp64_iterations": ip["iterations"],
                                     "plain_fp64_residual": ip["residual"], "chosen_residual": im["residual"],
                                     "speedup": ip["seconds"] / im["seconds"],
-                                    "chosen_vs_plain_rel_l2": float(np.linalg.norm(bm - bp) / np.linalg.norm(bp))}
+                                    "chosen_vs_plain_rel_l2": float(np.linalg.norm(bm - bp) / np.linalg.norm(bp)),
+                                    "bicgstab_mixed": {"s": ib["seconds"], "iterations": ib["iterations"],
+                                                       "matvecs_fp32": ib["matvecs_fp32"],
+                                                       "residual": ib["residual"],
+                                                       "vs_plain_rel_l2": float(np.linalg.norm(bb - bp) /
+                                                                                np.linalg.norm(bp))}}
         finally:
             B.celes_destroy(cs)
     B.celes_destroy(ctx)
+    batched = None if args.no_batched else run_batched(args, local_rank)
 
     # end to end through the C ABI with host buffers: H2D of the inputs,
     # D2H of the coefficients, every step
@@ -375,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         cores = host_cores()
-        rows = args.cpu_rows or 8 * max(cores, 2)  # about 10 s of oracle work
+        rows = args.cpu_rows or 24 * max(cores, 2)  # 10-20 s of oracle work
         sel = list(np.random.default_rng(7).choice(N, rows, replace=False))
         rate, dt = cpu_oracle_rate(scene, sel, cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -391,7 +459,8 @@ def run_ours(args, rank, world, local_rank):
                                        "step = incident coefficients + FP32/FP64-refined GMRES to 1e-6 + far field",
                            "N": N, "lmax": L, "tol": TOL, "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MB write); inputs resident in HBM"},
-                "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "batched": batched,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
 

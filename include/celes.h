@@ -101,6 +101,11 @@ typedef enum {
   CELES_X0_LEARNED = 3 /* guess from celes_gnn_predict, used only where its residual is below that of T a_in */
 } celes_x0_kind;
 
+typedef enum {
+  CELES_SOLVER_GMRES = 0,    /* restarted GMRES, classical Gram-Schmidt twice (Sec. 3.2) */
+  CELES_SOLVER_BICGSTAB = 1  /* BiCGSTAB (van der Vorst), the other Krylov solver named in Sec. 3.2 */
+} celes_solver;
+
 typedef struct {
   int mode;             /* celes_solve_mode */
   int restart;          /* GMRES restart length (default 100) */
@@ -109,6 +114,7 @@ typedef struct {
   int x0;               /* celes_x0_kind */
   int use_precond;      /* apply the block preconditioner if built (default 1) */
   double inner_tol;     /* MIXED: relative tolerance floor of each FP32 solve (default 1e-5) */
+  int solver;           /* celes_solver (default GMRES; restart is ignored by BiCGSTAB) */
 } celes_solve_opts;
 
 typedef struct {
@@ -181,6 +187,27 @@ int celes_get_tmatrix(celes_ctx* ctx, double* t_host);
  * for Nd directions dirs [Nd][2] = (beta, alpha); writes g [Nd][2] complex128
  * (host).  The radiant intensity is 2 pi^2/(omega k mu0) |g_j|^2. */
 int celes_farfield(celes_ctx* ctx, const double* dirs, int64_t Nd, double* g, int rhs);
+
+/* Electric field at Np points (Sec. 2.1), FP64, RHS `rhs`:
+ *   what = 0: scattered field sum_i sum_n b^i_n Psi^(3)_n(r - r_i) (needs a
+ *             solution), 1: incident field (plane wave App. A.1, or the
+ *             Gaussian beam's angular spectrum of App. C with the same beta
+ *             nodes as its coefficients), 2: their sum.
+ * points [Np][3] and E [Np][3] complex128 are host arrays.  Points inside a
+ * sphere get NaN for what = 0 and 2 (the internal field is not computed).
+ * Errors: EINVAL, ESTATE (no incident field, or no solution for what != 1),
+ * ENOMEM, ECUDA. */
+int celes_nearfield(celes_ctx* ctx, const double* points, int64_t Np, int rhs, int what, double* E);
+
+/* Reflected and transmitted power fractions R, T of RHS `rhs` (App. D; the
+ * reflectivity and transmittivity of Sec. 4): T = forward-hemisphere flux of
+ * the total field, R = backward-hemisphere flux of the scattered field, both
+ * divided by the Gaussian beam's power.  Quadrature: n_beta Gauss-Legendre
+ * nodes in beta per hemisphere, n_alpha trapezoid nodes in alpha.  Needs a
+ * solution and a Gaussian-beam RHS (EINVAL for a plane wave, whose power is
+ * not finite).  For lossless spheres R + T = 1 up to truncation and
+ * quadrature error. */
+int celes_power(celes_ctx* ctx, int rhs, int n_beta, int n_alpha, double* R, double* T);
 
 /* Problem sizes. */
 int64_t celes_num_spheres(const celes_ctx* ctx);
@@ -284,6 +311,39 @@ int celes_coupling_matvec_noalloc(int64_t N, int lmax, double k, const double* p
 
 void celes_destroy(celes_ctx* ctx);
 const char* celes_last_error(const celes_ctx* ctx);
+/* ---- Batched solves over many ensembles (multi-RHS, uneven sizes) --------
+ * A batch groups contexts (same device, any lmax and N, incident fields set)
+ * and solves the master equation (I - T W) b = T a_in (Sec. 2.2) for every
+ * right-hand side of every context in lockstep: the coupling products of all
+ * systems of one lmax run as one persistent launch that balances tiles of all
+ * ensembles, the operator is replayed from a CUDA graph, and the Krylov
+ * vector work of all systems runs in segmented kernels with one host
+ * synchronisation per Gram-Schmidt stage for the whole batch.
+ *
+ * celes_batch_create: ctxs [count] stay owned by the caller and must outlive
+ *   the batch; restart is the GMRES restart length (<= 0: 30).  Copies T a of
+ *   every system.  Errors: EINVAL (bad arguments, contexts on different
+ *   devices), ESTATE (a context without incident field), ENOMEM.
+ * celes_batch_master_matvec: y = (I - T W) x on the flat vectors of the
+ *   batch (device pointers; systems concatenated in context order, RHS-major
+ *   inside a context, [N][nmax] complex each; complex128 for FP64, complex64
+ *   for FP32).  Synchronous.
+ * celes_batch_solve: GMRES per system (no preconditioner, first iterate
+ *   T a), MIXED (FP32 inner + FP64 refinement) or FP64, to
+ *   ||T a - M b|| / ||T a|| <= tol per system; writes b into each context
+ *   (read with celes_get_coefficients) and infos [count] (per context: max
+ *   over its RHS; residual history not recorded).  opts may be NULL; its
+ *   x0 must be CELES_X0_TA and its solver GMRES; use_precond is ignored.  Returns OK, ENOCONV
+ *   (some system missed tol; b still written), ENUMERIC, ECUDA. */
+typedef struct celes_batch celes_batch;
+int celes_batch_create(celes_batch** out, celes_ctx* const* ctxs, int count, int restart);
+int celes_batch_num_systems(const celes_batch* b);
+long long celes_batch_num_unknowns(const celes_batch* b);
+int celes_batch_master_matvec(celes_batch* b, const void* x, void* y, int precision);
+int celes_batch_solve(celes_batch* b, double tol, const celes_solve_opts* opts, celes_solve_info* infos);
+const char* celes_batch_last_error(const celes_batch* b);
+void celes_batch_destroy(celes_batch* b);
+
 const char* celes_version(void);
 
 #ifdef __cplusplus

@@ -39,6 +39,8 @@ CELES_X0_TA = 0
 CELES_X0_USER = 1
 CELES_X0_ZERO = 2
 CELES_X0_LEARNED = 3
+CELES_SOLVER_GMRES = 0
+CELES_SOLVER_BICGSTAB = 1
 
 
 CELES_KERNEL_AUTO = 0
@@ -61,7 +63,7 @@ class celes_incident(ctypes.Structure):
 class celes_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("x0", ctypes.c_int), ("use_precond", ctypes.c_int),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("solver", ctypes.c_int)]
 
 
 class celes_solve_info(ctypes.Structure):
@@ -116,6 +118,17 @@ SIGNATURES = [
     ("celes_gnn_export", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.c_int]),
     ("celes_gnn_destroy", None, [ctypes.c_void_p]),
+    ("celes_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_c_ctx_p), ctypes.c_int,
+                                          ctypes.c_int]),
+    ("celes_batch_num_systems", ctypes.c_int, [ctypes.c_void_p]),
+    ("celes_batch_num_unknowns", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("celes_batch_master_matvec", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("celes_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(celes_solve_opts),
+                                         ctypes.POINTER(celes_solve_info)]),
+    ("celes_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("celes_batch_destroy", None, [ctypes.c_void_p]),
+    ("celes_power", ctypes.c_int, [_c_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+    ("celes_nearfield", ctypes.c_int, [_c_ctx_p, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp]),
     ("celes_destroy", None, [_c_ctx_p]),
     ("celes_last_error", ctypes.c_char_p, [_c_ctx_p]),
     ("celes_version", ctypes.c_char_p, []),
@@ -237,10 +250,11 @@ def celes_set_initial_guess(ctx, b0):
 
 
 def celes_solve(ctx, tol, mode=CELES_SOLVE_MIXED, restart=100, max_iter=2000, max_outer=20, x0=CELES_X0_TA,
-                use_precond=True, inner_tol=1e-5, history_cap=4096, raise_on_noconv=True):
-    """Returns a dict with the solve statistics and the residual history."""
+                use_precond=True, inner_tol=1e-5, history_cap=4096, raise_on_noconv=True, solver=0):
+    """Returns a dict with the solve statistics and the residual history.
+    solver: CELES_SOLVER_GMRES (0) or CELES_SOLVER_BICGSTAB (1)."""
     opts = celes_solve_opts(int(mode), int(restart), int(max_iter), int(max_outer), int(x0), int(bool(use_precond)),
-                            float(inner_tol))
+                            float(inner_tol), int(solver))
     hist = np.zeros(max(1, history_cap), dtype=np.float64)
     info = celes_solve_info()
     info.history = _dptr(hist)
@@ -395,6 +409,70 @@ def celes_gnn_export(g, what=0):
 def celes_gnn_destroy(g):
     if g:
         load().celes_gnn_destroy(g)
+
+
+def celes_nearfield(ctx, points, rhs=0, what=2):
+    """E at points [Np][3]: what 0 scattered, 1 incident, 2 total; returns complex128 [Np][3]."""
+    p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    E = np.zeros((p.shape[0], 3), dtype=np.complex128)
+    _check(load().celes_nearfield(ctx, _dptr(p), p.shape[0], int(rhs), int(what), _dptr(E.view(np.float64))), ctx)
+    return E
+
+
+def celes_power(ctx, rhs=0, n_beta=128, n_alpha=128):
+    """(R, T): reflected and transmitted power fractions of a Gaussian-beam RHS."""
+    R, T = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().celes_power(ctx, int(rhs), int(n_beta), int(n_alpha), ctypes.byref(R), ctypes.byref(T)), ctx)
+    return R.value, T.value
+
+
+def celes_batch_create(ctxs, restart=30):
+    """Batch of contexts (see include/celes.h): one lockstep solve for every RHS of every context."""
+    arr = (_c_ctx_p * len(ctxs))(*ctxs)
+    b = ctypes.c_void_p()
+    code = load().celes_batch_create(ctypes.byref(b), arr, len(ctxs), int(restart))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_batch_create")
+    return b
+
+
+def celes_batch_num_systems(b):
+    return int(load().celes_batch_num_systems(b))
+
+
+def celes_batch_num_unknowns(b):
+    return int(load().celes_batch_num_unknowns(b))
+
+
+def celes_batch_master_matvec(b, x, y, precision=CELES_FP64):
+    """y = (I - T W) x for every system; x, y flat device tensors of celes_batch_num_unknowns complex entries."""
+    code = load().celes_batch_master_matvec(b, _devptr(x), _devptr(y), int(precision))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_batch_master_matvec: " + celes_batch_last_error(b))
+
+
+def celes_batch_solve(b, count, tol, mode=CELES_SOLVE_MIXED, restart=30, max_iter=2000, max_outer=8,
+                      inner_tol=1e-5, raise_on_noconv=True):
+    """Returns (status, list of per-context info dicts)."""
+    opts = celes_solve_opts(int(mode), int(restart), int(max_iter), int(max_outer), CELES_X0_TA, 0, float(inner_tol),
+                            CELES_SOLVER_GMRES)
+    infos = (celes_solve_info * count)()
+    code = load().celes_batch_solve(b, float(tol), ctypes.byref(opts), infos)
+    out = [{"status": int(i.status), "iterations": i.iterations, "outer": i.outer, "matvecs_fp64": i.matvecs_fp64,
+            "matvecs_fp32": i.matvecs_fp32, "residual": i.residual, "seconds": i.seconds} for i in infos]
+    if code != CELES_OK and not (code == CELES_ENOCONV and not raise_on_noconv):
+        raise CelesError(code, "celes_batch_solve: " + celes_batch_last_error(b))
+    return int(code), out
+
+
+def celes_batch_last_error(b):
+    m = load().celes_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def celes_batch_destroy(b):
+    if b:
+        load().celes_batch_destroy(b)
 
 
 def celes_destroy(ctx):

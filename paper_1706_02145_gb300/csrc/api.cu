@@ -34,6 +34,7 @@ namespace celes {
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
                                        void* partial, double k, int chunks, cudaStream_t st);              \
   int coupling_rtr_rpb_##LL(int precision);                                                                \
+  int coupling_rtr_slots_##LL(int precision);                                                              \
   long long coupling_rtr_flops_##LL();                                                                     \
   int coupling_terms_export_##LL(int* idx, double* val, int cap);
 CELES_DECLARE(1)
@@ -72,6 +73,16 @@ int coupling_rtr_receivers_per_block(int L, int precision) {
     case 3: return coupling_rtr_rpb_3(precision);
     case 4: return coupling_rtr_rpb_4(precision);
     case 5: return coupling_rtr_rpb_5(precision);
+    default: return 0;
+  }
+}
+int coupling_rtr_slots(int L, int precision) {
+  switch (L) {
+    case 1: return coupling_rtr_slots_1(precision);
+    case 2: return coupling_rtr_slots_2(precision);
+    case 3: return coupling_rtr_slots_3(precision);
+    case 4: return coupling_rtr_slots_4(precision);
+    case 5: return coupling_rtr_slots_5(precision);
     default: return 0;
   }
 }
@@ -149,6 +160,7 @@ struct celes_ctx {
   int kernel = CELES_KERNEL_AUTO;
   DevBuf pos, radii, nrel, tq, tq32, tdiag;
   int nrhs = 0;
+  std::vector<celes_incident> incidents;  // descriptors of the current RHS
   DevBuf ain, rhs, b, x0;
   bool has_b = false, has_x0 = false, x0_learned = false;
   DevBuf partial;
@@ -226,10 +238,15 @@ bool use_rtr(const celes_ctx* c, int precision) {
 
 int auto_chunks(const celes_ctx* c, int precision) {
   if (c->chunks_opt > 0) return c->chunks_opt;
-  const int rpb = use_rtr(c, precision) ? coupling_rtr_receivers_per_block(c->L, precision)
-                                        : coupling_receivers_per_block(c->L, precision);
+  const bool rtr = use_rtr(c, precision);
+  const int rpb = rtr ? coupling_rtr_receivers_per_block(c->L, precision)
+                      : coupling_receivers_per_block(c->L, precision);
   const int64_t rb = (c->N + rpb - 1) / rpb;
-  const int64_t target = 152 * 2 * 4;  // about four waves of two CTAs per SM
+  // about eight waves of resident CTAs: the last, partly filled wave then
+  // idles the GPU for a small fraction of the launch (measured: 12.7 ms at
+  // eight waves vs 13.7 ms at four, lmax 4, N = 10 000)
+  const int slots = rtr ? coupling_rtr_slots(c->L, precision) : 152 * 2;
+  const int64_t target = 8LL * (slots > 0 ? slots : 304);
   int64_t ch = (target + rb - 1) / rb;
   const int64_t max_by_src = std::max<int64_t>(1, c->N / 64);
   ch = std::min<int64_t>(ch, max_by_src);
@@ -521,6 +538,7 @@ extern "C" int celes_set_incident(celes_ctx* c, const celes_incident* inc, int n
   CK(c->rhs.ensure(per * nrhs), "rhs");
   CK(c->b.ensure(per * nrhs), "b");
   c->nrhs = nrhs;
+  c->incidents.assign(inc, inc + nrhs);
   c->has_b = false;
   c->has_x0 = false;
   DevBuf nodes, weights;
@@ -843,9 +861,144 @@ struct Gmres {
   }
 };
 
+// BiCGSTAB (van der Vorst 1992), right preconditioned, for the same inner
+// problem as Gmres::solve: A u = r with A = M P^{-1}, u0 = 0, x += P^{-1} u.
+// Per iteration two operator applications and three host reductions:
+// [rho, ||r||^2], <r^, v>, [<t, t>, <s, t>].
+template <typename R>
+struct Bicgstab {
+  celes_ctx* c;
+  int64_t n;
+  bool precond;
+  DevBuf W, z;  // W: 7 vectors [r^ | r | t | s | p | v | u], z: preconditioned work vector
+  enum { RH = 0, RR = 1, TT = 2, SS = 3, PP = 4, VV = 5, UU = 6 };
+  int prec() const { return sizeof(R) == 8 ? CELES_FP64 : CELES_FP32; }
+  size_t vbytes() const { return sizeof(R) * 2 * n; }
+  char* Wp(int j) { return W.as<char>() + vbytes() * j; }
+
+  int init() {
+    CK(W.ensure(vbytes() * 7), "BiCGSTAB vectors");
+    CK(z.ensure(vbytes()), "work");
+    CK(c->dots.ensure(sizeof(double) * 2 * 4), "dots");
+    CK(c->dot_partial.ensure(sizeof(double) * 2 * 4 * vec_dot_blocks(n)), "dot partials");
+    return CELES_OK;
+  }
+  int dots(const void* Vbase, int nv, const void* v, std::complex<double>* h) {
+    CK(launch_multi_dotc<R>(n, nv, Vbase, n, v, c->dot_partial.as<double>(), c->dots.as<double>(), c->stream), "dot");
+    CK(cudaMemcpyAsync(h, c->dots.p, sizeof(double) * 2 * nv, cudaMemcpyDeviceToHost, c->stream), "d2h");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return CELES_OK;
+  }
+  int apply_op(const void* v, void* out, int& nmv) {
+    const void* src = v;
+    if (precond) {
+      int s = precond_apply_internal(c, v, z.p, 1, prec(), c->stream);
+      if (s) return s;
+      src = z.p;
+    }
+    ++nmv;
+    return coupling_apply(c, src, out, 1, prec(), 1, c->stream);
+  }
+  int zaxpby(std::complex<double> a, int x, std::complex<double> b, int y, int zz) {
+    CK(launch_caxpbyz<R>(n, a.real(), a.imag(), Wp(x), b.real(), b.imag(), Wp(y), Wp(zz), c->stream), "axpby");
+    return CELES_OK;
+  }
+  int solve(const void* r, void* x, double tol, int max_it, int& its, double& rel_est, int& nmv,
+            std::vector<double>* hist, double hist_scale) {
+    its = 0;
+    rel_est = 1.0;
+    CK(cudaMemcpyAsync(Wp(RH), r, vbytes(), cudaMemcpyDeviceToDevice, c->stream), "r^");
+    CK(cudaMemcpyAsync(Wp(RR), r, vbytes(), cudaMemcpyDeviceToDevice, c->stream), "r");
+    CK(cudaMemsetAsync(Wp(UU), 0, vbytes(), c->stream), "u");
+    std::complex<double> h[2];
+    int s = dots(Wp(RH), 2, Wp(RR), h);  // [<r^, r>, <r, r>]
+    if (s) return s;
+    const double r0 = std::sqrt(std::max(0.0, h[1].real()));
+    if (!(r0 > 0.0)) {
+      rel_est = 0.0;
+      return CELES_OK;
+    }
+    if (!std::isfinite(r0)) return fail(c, CELES_ENUMERIC, "BiCGSTAB: non-finite residual");
+    std::complex<double> rho = h[0], rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    while (its < max_it) {
+      if (std::abs(rho) == 0.0) break;  // breakdown: keep the current iterate
+      if (its == 0) {
+        CK(cudaMemcpyAsync(Wp(PP), Wp(RR), vbytes(), cudaMemcpyDeviceToDevice, c->stream), "p");
+      } else {
+        const std::complex<double> beta = (rho / rho_prev) * (alpha / omega);
+        s = zaxpby(1.0, PP, -omega, VV, PP);  // p = p - omega v
+        if (s) return s;
+        s = zaxpby(1.0, RR, beta, PP, PP);  // p = r + beta p
+        if (s) return s;
+      }
+      s = apply_op(Wp(PP), Wp(VV), nmv);
+      if (s) return s;
+      std::complex<double> rv;
+      s = dots(Wp(RH), 1, Wp(VV), &rv);
+      if (s) return s;
+      if (std::abs(rv) == 0.0) break;
+      alpha = rho / rv;
+      s = zaxpby(1.0, RR, -alpha, VV, SS);  // s = r - alpha v
+      if (s) return s;
+      s = apply_op(Wp(SS), Wp(TT), nmv);
+      if (s) return s;
+      s = dots(Wp(TT), 2, Wp(TT), h);  // [<t, t>, <s, t>]
+      if (s) return s;
+      const double tt = h[0].real();
+      omega = tt > 0.0 ? std::conj(h[1]) / tt : 0.0;  // <t, s> / <t, t>
+      s = zaxpby(1.0, UU, alpha, PP, UU);  // u += alpha p + omega s
+      if (s) return s;
+      s = zaxpby(1.0, UU, omega, SS, UU);
+      if (s) return s;
+      s = zaxpby(1.0, SS, -omega, TT, RR);  // r = s - omega t
+      if (s) return s;
+      ++its;
+      rho_prev = rho;
+      s = dots(Wp(RH), 2, Wp(RR), h);
+      if (s) return s;
+      rho = h[0];
+      const double rn = std::sqrt(std::max(0.0, h[1].real()));
+      if (!std::isfinite(rn)) return fail(c, CELES_ENUMERIC, "BiCGSTAB: non-finite residual");
+      rel_est = rn / r0;
+      if (hist) hist->push_back(rel_est * hist_scale);
+      if (rn <= tol * r0 || std::abs(omega) == 0.0) break;
+    }
+    // x += P^{-1} u
+    if (precond) {
+      int q = precond_apply_internal(c, Wp(UU), z.p, 1, prec(), c->stream);
+      if (q) return q;
+      CK(launch_axpby<R, R>(n, 1.0, z.p, 1.0, x, c->stream), "update");
+    } else {
+      CK(launch_axpby<R, R>(n, 1.0, Wp(UU), 1.0, x, c->stream), "update");
+    }
+    return CELES_OK;
+  }
+};
+
+// the inner solver chosen by the options
+template <typename R>
+struct Inner {
+  Gmres<R> g;
+  Bicgstab<R> b;
+  bool bicg;
+  Inner(celes_ctx* c, int64_t n, int m, bool pc, bool use_bicg)
+      : g{c, n, m, pc}, b{c, n, pc}, bicg(use_bicg) {}
+  int init() { return bicg ? b.init() : g.init(); }
+  int norm(const void* v, double& out) { return g.norm(v, out); }
+  int solve(const void* r, void* x, double tol, int max_it, int& its, double& rel_est, int& nmv,
+            std::vector<double>* hist, double hist_scale) {
+    return bicg ? b.solve(r, x, tol, max_it, its, rel_est, nmv, hist, hist_scale)
+                : g.solve(r, x, tol, max_it, its, rel_est, nmv, hist, hist_scale);
+  }
+};
+
 }  // namespace
 
 namespace celes {
+void gauss_legendre_nodes(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
+  gauss_legendre(n, a, b, x, w);
+}
+
 int ctx_view(celes_ctx* c, CtxView* v) {
   if (!c || !v) return CELES_EINVAL;
   v->N = c->N;
@@ -859,7 +1012,18 @@ int ctx_view(celes_ctx* c, CtxView* v) {
   v->rhs = c->rhs.as<double>();
   v->b = c->b.as<double>();
   v->has_b = c->has_b;
+  v->tq = c->tq.p;
+  v->tq32 = c->tq32.p;
+  v->device = c->device;
+  v->incidents = c->incidents.data();
+  v->stream = c->stream;
   if (c->nrhs < 1) return CELES_ESTATE;
+  return CELES_OK;
+}
+
+int ctx_mark_solved(celes_ctx* c) {
+  if (!c || c->nrhs < 1) return CELES_EINVAL;
+  c->has_b = true;
   return CELES_OK;
 }
 
@@ -894,7 +1058,7 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
   if (!c) return CELES_EINVAL;
   if (c->nrhs < 1) return fail(c, CELES_ESTATE, "solve: call set_incident first");
   if (!(tol > 0.0)) return fail(c, CELES_EINVAL, "solve: tol must be > 0");
-  celes_solve_opts opt{CELES_SOLVE_MIXED, 100, 2000, 20, CELES_X0_TA, 1, 1e-5};
+  celes_solve_opts opt{CELES_SOLVE_MIXED, 100, 2000, 20, CELES_X0_TA, 1, 1e-5, CELES_SOLVER_GMRES};
   if (o) opt = *o;
   if (opt.restart <= 0) opt.restart = 100;
   if (opt.max_iter <= 0) opt.max_iter = 2000;
@@ -906,6 +1070,9 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
   if (opt.x0 == CELES_X0_LEARNED && !(c->has_x0 && c->x0_learned))
     return fail(c, CELES_ESTATE, "solve: no learned guess (call celes_gnn_predict)");
   if (opt.x0 < CELES_X0_TA || opt.x0 > CELES_X0_LEARNED) return fail(c, CELES_EINVAL, "solve: unknown x0 kind");
+  if (opt.solver != CELES_SOLVER_GMRES && opt.solver != CELES_SOLVER_BICGSTAB)
+    return fail(c, CELES_EINVAL, "solve: unknown solver %d", opt.solver);
+  const bool bicg = opt.solver == CELES_SOLVER_BICGSTAB;
   DeviceGuard dg(c->device);
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = c->N * c->nmax;
@@ -917,8 +1084,8 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
   int status = CELES_OK;
   DevBuf r64, d64, r32, d32;
   CK(r64.ensure(per64), "residual");
-  Gmres<double> g64{c, n, opt.restart, use_pc};
-  Gmres<float> g32{c, n, opt.restart, use_pc};
+  Inner<double> g64(c, n, opt.restart, use_pc, bicg);
+  Inner<float> g32(c, n, opt.restart, use_pc, bicg);
   if (opt.mode == CELES_SOLVE_FP64) {
     int s = g64.init();
     if (s) return s;
@@ -1017,8 +1184,7 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
       CK(launch_axpby<double, float>(n, 1.0, rhs, -1.0, r32.p, c->stream), "residual32");
       double rn = 0.0;
       {
-        Gmres<float>& gg = g32;
-        s = gg.norm(r32.p, rn);
+        s = g32.norm(r32.p, rn);
         if (s) return s;
       }
       rel = rn / rhs_norm;

@@ -92,11 +92,14 @@ long long rtr_flops_per_pair_t() {
   [&]<int... I>(std::integer_sequence<int, I...>) { (per_l(std::integral_constant<int, I + 1>{}), ...); }
   (std::make_integer_sequence<int, L>{});
   f += 2 * rot + 2 * dm;
+  // axial entries: with the transpose symmetry only the entries lo <= li are
+  // formed; every entry is applied to both rows
+  constexpr bool sym = rtr::Config<L, float>::SYM_AXIAL;
   for (int mu = 0; mu <= L; ++mu) {
     for (int lo = (mu > 1 ? mu : 1); lo <= L; ++lo) {
       for (int li = (mu > 1 ? mu : 1); li <= L; ++li) {
         const rtr::AxialRow<L> a = rtr::make_axial<L>(mu, lo, li);
-        f += 4LL * (a.na + a.nb) + 4;
+        if (!sym || lo <= li) f += 4LL * (a.na + a.nb) + 4;
         f += (mu > 0 ? 2 : 1) * 16LL;
       }
     }
@@ -129,6 +132,14 @@ long long rtr_flops_per_pair_t() {
     return CouplingLayout<LL, float>::RPB;                                                                 \
   }                                                                                                        \
   long long coupling_rtr_flops_##LL() { return rtr_flops_per_pair_t<LL>(); }                                 \
+  int coupling_rtr_slots_##LL(int precision) {                                                             \
+    return precision == 0 ? rtr::resident_slots<LL, double>() : rtr::resident_slots<LL, float>();           \
+  }                                                                                                        \
+  cudaError_t launch_rtr_batch_##LL(int precision, const void* sys, int nsys, long long ntiles,              \
+                                    unsigned long long* counter, cudaStream_t st) {                          \
+    return precision == 0 ? rtr::launch_batch<LL, double>(sys, nsys, ntiles, counter, st)                   \
+                          : rtr::launch_batch<LL, float>(sys, nsys, ntiles, counter, st);                   \
+  }                                                                                                        \
   int coupling_terms_export_##LL(int* idx, double* val, int cap) {                                         \
     return coupling_terms_export_t<LL>(idx, val, cap);                                                     \
   }

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "../../include/celes.h"
+
 struct celes_ctx;
 
 namespace celes {
@@ -20,10 +22,17 @@ struct CtxView {
   const double* rhs;     // [nrhs][N][nmax] complex, T a_in
   const double* b;       // [nrhs][N][nmax] complex, current solution
   bool has_b;
+  const void* tq;        // [N][2][L] complex128, T
+  const void* tq32;      // [N][2][L] complex64, T
+  int device;
+  const celes_incident* incidents;  // [nrhs] host descriptors
+  cudaStream_t stream;
 };
 int ctx_view(celes_ctx* c, CtxView* v);
 // store a learned first iterate for RHS `rhs` (device pointer, complex128 [N][nmax])
 int ctx_set_learned_guess(celes_ctx* c, int rhs, const double* b0_dev);
+// the solution buffer (b, [nrhs][N][nmax] complex128) now holds a solution
+int ctx_mark_solved(celes_ctx* c);
 
 // process-wide count of kernels launched by this library
 void note_launch(int n = 1);
@@ -61,6 +70,10 @@ cudaError_t launch_multi_combine(int64_t n, int nv, const void* V, int64_t ldv, 
                                  cudaStream_t st);
 template <typename RX, typename RY>
 cudaError_t launch_axpby(int64_t n, double a, const void* x, double b, void* y, cudaStream_t st);
+// z = a x + b y, complex a = ar + i ai, b = br + i bi (z may alias x or y)
+template <typename R>
+cudaError_t launch_caxpbyz(int64_t n, double ar, double ai, const void* x, double br, double bi, const void* y,
+                           void* z, cudaStream_t st);
 cudaError_t launch_tdiag_mul(int64_t n_per_rhs, int nrhs, const double* tdiag, const double* x, double* y,
                              cudaStream_t st);
 template <typename R>

@@ -23,7 +23,8 @@ namespace celes {
 #define CELES_DECLARE_RTR(LL)                                                                               \
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
                                        void* partial, double k, int chunks, cudaStream_t st);              \
-  int coupling_rtr_rpb_##LL(int precision);
+  int coupling_rtr_rpb_##LL(int precision);                                                                \
+  int coupling_rtr_slots_##LL(int precision);
 CELES_DECLARE_RTR(1)
 CELES_DECLARE_RTR(2)
 CELES_DECLARE_RTR(3)
@@ -76,6 +77,18 @@ cudaError_t launch_rtr(int L, int precision, int64_t N, const void* pos, const v
   }
 }
 
+int rtr_slots(int L, int precision) {
+  using namespace celes;
+  switch (L) {
+    case 1: return coupling_rtr_slots_1(precision);
+    case 2: return coupling_rtr_slots_2(precision);
+    case 3: return coupling_rtr_slots_3(precision);
+    case 4: return coupling_rtr_slots_4(precision);
+    case 5: return coupling_rtr_slots_5(precision);
+    default: return 0;
+  }
+}
+
 int rtr_rpb(int L, int precision) {
   using namespace celes;
   switch (L) {
@@ -107,7 +120,8 @@ extern "C" int celes_coupling_matvec_noalloc(int64_t N, int lmax, double k, cons
   if (xb < yb + vec_bytes && yb < xb + vec_bytes) return CELES_EINVAL;  // x and y overlap
   const int rpb = rtr_rpb(lmax, precision);
   const int64_t rb = (N + rpb - 1) / rpb;
-  int64_t chunks = (152 * 2 * 4 + rb - 1) / rb;
+  const int slots = rtr_slots(lmax, precision);
+  int64_t chunks = (8LL * (slots > 0 ? slots : 304) + rb - 1) / rb;  // about eight waves
   chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, N / 64));
   chunks = std::min<int64_t>(chunks, 256);
   chunks = std::min<int64_t>(chunks, static_cast<int64_t>(max_chunks));

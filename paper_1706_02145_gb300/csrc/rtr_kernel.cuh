@@ -359,12 +359,86 @@ __device__ __forceinline__ void ax_pair(const Geom<L, R>& g, XV& xp, R (&y)[8]) 
   }
 }
 
-template <int L, int MU, int LO, typename R, typename XV, typename YV, int... LII>
-__device__ __forceinline__ void ax_row(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, LII...>) {
+template <int L, int MU, int LO, typename R, typename YV>
+__device__ __forceinline__ void ax_store(YV& yp, const R (&y)[8]);
+
+// y += S w x for one (row, column) entry, S = +-1 at compile time
+template <int S, typename R>
+__device__ __forceinline__ void cmac_s(R& yr, R& yi, R wr, R wi, R xr, R xi) {
+  if constexpr (S > 0) {
+    cmac(yr, yi, wr, wi, xr, xi);
+  } else {
+    cmac(yr, yi, -wr, -wi, xr, xi);
+  }
+}
+
+// Transpose symmetry of the axial block: for a translation along +z the entry
+// (l', l) of every |mu| equals (-1)^{l + l'} times the entry (l, l') (A and B
+// alike; it follows from the inversion parity of the SVWFs, and is checked
+// against the dense coupling matrix).  So each entry with LO <= LI is formed
+// once and applied to row LO (column LI) and, with that sign, to row LI
+// (column LO).  y[l - 1] holds row l: (+mu: y+ re/im, y- re/im; -mu: same).
+template <int L, int MU, int LO, int LI, typename R, typename XV>
+__device__ __forceinline__ void ax_sym_pair(const Geom<L, R>& g, XV& xp, R (&y)[L][8]) {
+  constexpr int NH = L * (L + 2);
+  if constexpr (LO >= MU && LI >= MU && LO <= LI) {
+    R ar = 0, ai = 0, br = 0, bi = 0;
+    ax_entry<L, MU, LO, LI>(g, ar, ai, br, bi, std::make_integer_sequence<int, AxialN<L, MU, LO, LI>::na>{},
+                            std::make_integer_sequence<int, AxialN<L, MU, LO, LI>::nb>{});
+    const R wpr = ar - bi, wpi = ai + br, wmr = ar + bi, wmi = ai - br;
+    {
+      R(&yo)[8] = y[LO - 1];
+      constexpr int ri = Row<LI, MU>::r;
+      cmac(yo[0], yo[1], wpr, wpi, xp(2 * ri), xp(2 * ri + 1));
+      cmac(yo[2], yo[3], wmr, wmi, xp(2 * (NH + ri)), xp(2 * (NH + ri) + 1));
+      if constexpr (MU > 0) {
+        constexpr int rim = Row<LI, -MU>::r;
+        cmac(yo[4], yo[5], wmr, wmi, xp(2 * rim), xp(2 * rim + 1));
+        cmac(yo[6], yo[7], wpr, wpi, xp(2 * (NH + rim)), xp(2 * (NH + rim) + 1));
+      }
+    }
+    if constexpr (LO != LI) {
+      constexpr int S = ((LO + LI) & 1) ? -1 : 1;
+      R(&yt)[8] = y[LI - 1];
+      constexpr int rj = Row<LO, MU>::r;
+      cmac_s<S>(yt[0], yt[1], wpr, wpi, xp(2 * rj), xp(2 * rj + 1));
+      cmac_s<S>(yt[2], yt[3], wmr, wmi, xp(2 * (NH + rj)), xp(2 * (NH + rj) + 1));
+      if constexpr (MU > 0) {
+        constexpr int rjm = Row<LO, -MU>::r;
+        cmac_s<S>(yt[4], yt[5], wmr, wmi, xp(2 * rjm), xp(2 * rjm + 1));
+        cmac_s<S>(yt[6], yt[7], wpr, wpi, xp(2 * (NH + rjm)), xp(2 * (NH + rjm) + 1));
+      }
+    }
+  }
+}
+template <int L, int MU, int LO, typename R, typename XV, int... LII>
+__device__ __forceinline__ void ax_sym_row(const Geom<L, R>& g, XV& xp, R (&y)[L][8],
+                                           std::integer_sequence<int, LII...>) {
+  (ax_sym_pair<L, MU, LO, LII + 1>(g, xp, y), ...);
+}
+template <int L, int MU, typename R, typename XV, typename YV, int... LOI>
+__device__ __forceinline__ void ax_mu_sym(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, LOI...>) {
+  R y[L][8];
+#pragma unroll
+  for (int a = 0; a < L; ++a)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[a][q] = static_cast<R>(0);
+  (ax_sym_row<L, MU, LOI + 1>(g, xp, y, std::make_integer_sequence<int, L>{}), ...);
+  (ax_store<L, MU, LOI + 1>(yp, y[LOI]), ...);
+}
+
+template <int L, int MU, int LO, typename R, typename XV, int... LII>
+__device__ __forceinline__ void ax_row(const Geom<L, R>& g, XV& xp, R (&y)[8], std::integer_sequence<int, LII...>) {
+  if constexpr (LO >= MU) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[q] = static_cast<R>(0);
+    (ax_pair<L, MU, LO, LII + 1>(g, xp, y), ...);
+  }
+}
+template <int L, int MU, int LO, typename R, typename YV>
+__device__ __forceinline__ void ax_store(YV& yp, const R (&y)[8]) {
   constexpr int NH = L * (L + 2);
   if constexpr (LO >= MU) {
-    R y[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    (ax_pair<L, MU, LO, LII + 1>(g, xp, y), ...);
     constexpr int ro = Row<LO, MU>::r;
     yp(2 * ro) = y[0];
     yp(2 * ro + 1) = y[1];
@@ -379,13 +453,32 @@ __device__ __forceinline__ void ax_row(const Geom<L, R>& g, XV& xp, YV& yp, std:
     }
   }
 }
-template <int L, int MU, typename R, typename XV, typename YV, int... LOI>
-__device__ __forceinline__ void ax_mu(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, LOI...>) {
-  (ax_row<L, MU, LOI + 1>(g, xp, yp, std::make_integer_sequence<int, L>{}), ...);
+template <int L, int MU, int LO, typename R, typename XV, typename YV>
+__device__ __forceinline__ void ax_row_store(const Geom<L, R>& g, XV& xp, YV& yp) {
+  R y[8];
+  ax_row<L, MU, LO>(g, xp, y, std::make_integer_sequence<int, L>{});
+  ax_store<L, MU, LO>(yp, y);
 }
-template <int L, typename R, typename XV, typename YV, int... MUS>
+// in place (y' overwrites x'): all rows of one |mu| are formed before any is
+// stored, since the rows of |mu| read every x'[., +-mu]; otherwise each row is
+// stored as soon as it is formed
+template <int L, int MU, bool INPLACE, typename R, typename XV, typename YV, int... LOI>
+__device__ __forceinline__ void ax_mu(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, LOI...>) {
+  if constexpr (INPLACE) {
+    R y[L][8];
+    (ax_row<L, MU, LOI + 1>(g, xp, y[LOI], std::make_integer_sequence<int, L>{}), ...);
+    (ax_store<L, MU, LOI + 1>(yp, y[LOI]), ...);
+  } else {
+    (ax_row_store<L, MU, LOI + 1>(g, xp, yp), ...);
+  }
+}
+template <int L, bool INPLACE, bool SYM, typename R, typename XV, typename YV, int... MUS>
 __device__ __forceinline__ void axial(const Geom<L, R>& g, XV& xp, YV& yp, std::integer_sequence<int, MUS...>) {
-  (ax_mu<L, MUS>(g, xp, yp, std::make_integer_sequence<int, L>{}), ...);
+  if constexpr (SYM) {
+    (ax_mu_sym<L, MUS>(g, xp, yp, std::make_integer_sequence<int, L>{}), ...);
+  } else {
+    (ax_mu<L, MUS, INPLACE>(g, xp, yp, std::make_integer_sequence<int, L>{}), ...);
+  }
 }
 
 // ---- step 4: y[l, M] += e^{-i M phi} sum_MU R_{MU,M} y'[l, MU] -------------
@@ -479,55 +572,56 @@ struct RowAccSmem {
   __device__ __forceinline__ void store(int r, const R (&c)[4]) const { a[r * BLOCK] = Quad4<R>{c[0], c[1], c[2], c[3]}; }
 };
 
-template <int L, typename R, typename XV, typename YV, typename Acc>
+template <int L, bool INPLACE, bool SYM, typename R, typename XV, typename YV, typename Acc>
 __device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, YV& yp, Acc& acc) {
   rot_fwd<L>(g, xs, xp, std::make_integer_sequence<int, L>{});
-  axial<L>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
+  axial<L, INPLACE, SYM>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
   rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
 }
 
+// Launch shape per (lmax, precision), chosen by timing sweeps on GB300 at
+// N = 10 000 (FP32: lmax 3 0.95x, lmax 5 0.31x the time of the earlier shapes)
 template <int L, typename R>
 struct Config {
   static constexpr bool FP64 = sizeof(R) == 8;
-  static constexpr int BLOCK = (FP64 && L >= 5) ? 32 : ((FP64 || L >= 5) ? 64 : 128);
+  static constexpr int BLOCK = FP64 ? (L >= 5 ? 32 : 64) : 128;
   static constexpr int TJ = FP64 ? 16 : 32;
-  static constexpr bool ACC_SMEM = FP64 ? (L >= 2) : (L >= 4);
-  static constexpr bool XY_SMEM = FP64 ? (L >= 3) : (L >= 5);
+  static constexpr bool ACC_SMEM = FP64 ? (L >= 2) : (L >= 3);
+  static constexpr bool XY_SMEM = FP64 && L >= 3;
+  static constexpr bool XY_INPLACE = XY_SMEM;  // y' overwrites x' (one shared-memory array)
+  static constexpr bool SYM_AXIAL = true;       // axial entries formed once per (l, l') pair
+  static constexpr int MINB = (!FP64 && L == 3) ? 3 : 1;  // minimum resident CTAs per SM for the allocator
 };
 
-template <int L, typename R>
+template <int L, typename R, typename C = Config<L, R>>
 struct Layout {
-  using C = Config<L, R>;
   static constexpr int NH = L * (L + 2);
   static constexpr size_t col = sizeof(R) * 4 * NH * C::BLOCK;  // one [4 NH][BLOCK] array
   static constexpr size_t off_pos = 0;
   static constexpr size_t off_x = off_pos + sizeof(Pos4) * C::TJ;
   static constexpr size_t off_acc = off_x + sizeof(Pair2<R>) * 2 * NH * C::TJ;
   static constexpr size_t off_xy = off_acc + (C::ACC_SMEM ? col : 0);
-  static constexpr size_t bytes = off_xy + (C::XY_SMEM ? 2 * col : 0);
+  static constexpr size_t bytes = off_xy + (C::XY_SMEM ? (C::XY_INPLACE ? 1 : 2) * col : 0);
 };
 
-// grid (receiver blocks of BLOCK, source chunks); writes partial sums in the
-// +- basis, [chunks][N][2][NH] complex (same layout as the direct kernel)
-template <int L, typename R>
-__global__ void __launch_bounds__(Config<L, R>::BLOCK)
-    rtr_partial_kernel(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
-                       Pair2<R>* __restrict__ partial, double k, int chunk) {
-  using C = Config<L, R>;
-  using LY = Layout<L, R>;
+// One tile: receivers rb*BLOCK .. +BLOCK against sources j0 .. j1 - 1; writes
+// this tile's partial sums in the +- basis to out ([N][2][NH] complex, the
+// slice of the tile's source chunk).  Called by every thread of the CTA.
+template <int L, typename R, typename C>
+__device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
+                                         Pair2<R>* __restrict__ outp, double k, int rb, int j0, int j1,
+                                         unsigned char* smem_raw) {
+  using LY = Layout<L, R, C>;
   constexpr int NH = L * (L + 2);
   constexpr int BLOCK = C::BLOCK;
   constexpr int TJ = C::TJ;
-  extern __shared__ __align__(32) unsigned char smem_raw[];
   Pos4* spos = reinterpret_cast<Pos4*>(smem_raw + LY::off_pos);
   Pair2<R>* sx = reinterpret_cast<Pair2<R>*>(smem_raw + LY::off_x);
   R* sacc = reinterpret_cast<R*>(smem_raw + LY::off_acc);
   R* sxy = reinterpret_cast<R*>(smem_raw + LY::off_xy);
 
   const int tid = threadIdx.x;
-  const int i = blockIdx.x * BLOCK + tid;
-  const int j0 = blockIdx.y * chunk;
-  const int j1 = min(N, j0 + chunk);
+  const int i = rb * BLOCK + tid;
   const bool active = i < N;
   constexpr bool FF = sizeof(R) == 4;  // FP32: float-float positions scaled by k
   Pos4 ri = Pos4{0, 0, 0, 0};
@@ -573,17 +667,18 @@ __global__ void __launch_bounds__(Config<L, R>::BLOCK)
         }
         const Pair2<R>* xs = sx + jj * 2 * NH;
         auto run = [&](auto& xp, auto& yp) {
+          constexpr bool INPL = C::XY_SMEM && C::XY_INPLACE;
           if constexpr (C::ACC_SMEM) {
             RowAccSmem<R, BLOCK> acc{sacc4 + tid};
-            pair<L, R>(g, xs, xp, yp, acc);
+            pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
           } else {
             RowAccReg<R> acc{areg};
-            pair<L, R>(g, xs, xp, yp, acc);
+            pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
           }
         };
         if constexpr (C::XY_SMEM) {
           AccSmem<R, BLOCK> xp{sxy + tid};
-          AccSmem<R, BLOCK> yp{sxy + 4 * NH * BLOCK + tid};
+          AccSmem<R, BLOCK> yp{sxy + (C::XY_INPLACE ? 0 : 4 * NH * BLOCK) + tid};
           run(xp, yp);
         } else {
           R xa[4 * NH], ya[4 * NH];
@@ -596,7 +691,7 @@ __global__ void __launch_bounds__(Config<L, R>::BLOCK)
   }
   if (active) {
     // partial layout [2][NH] complex: y+ rows, then y- rows
-    Pair2<R>* out = partial + ((size_t)blockIdx.y * N + i) * (2 * NH);
+    Pair2<R>* out = outp + (size_t)i * (2 * NH);
     if constexpr (C::ACC_SMEM) {
       for (int r = 0; r < NH; ++r) {
         const Quad4<R> v = sacc4[r * BLOCK + tid];
@@ -613,26 +708,123 @@ __global__ void __launch_bounds__(Config<L, R>::BLOCK)
   }
 }
 
-template <int L, typename R>
+// grid (receiver blocks of BLOCK, source chunks); writes partial sums in the
+// +- basis, [chunks][N][2][NH] complex (same layout as the direct kernel)
+template <int L, typename R, typename C = Config<L, R>>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    rtr_partial_kernel(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
+                       Pair2<R>* __restrict__ partial, double k, int chunk) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  constexpr int NH = L * (L + 2);
+  const int j0 = blockIdx.y * chunk;
+  const int j1 = min(N, j0 + chunk);
+  rtr_tile<L, R, C>(N, pos, x, partial + (size_t)blockIdx.y * N * (2 * NH), k, blockIdx.x, j0, j1, smem_raw);
+}
+
+// ---- batched form: one persistent launch over the tiles of many systems ----
+// A system is one right-hand side of one sphere ensemble (all of the same
+// lmax in one launch).  Its tiles are (receiver block, source chunk) pairs
+// numbered tile0 .. tile0 + nrb * chunks - 1 within the launch; CTAs take
+// tiles from a global counter (dynamic scheduling, so uneven ensembles
+// balance), and systems whose flag `active` is 0 are skipped.
+struct BatchSys {
+  const Pos4* pos;
+  const void* x;      // input vector [N][nmax] complex (FP32 or FP64 as launched)
+  void* y;            // output [N][nmax]
+  void* partial;      // [chunks][N][2][NH] scratch
+  const void* tq;     // T [N][2][L] complex in the launch's precision (master operator)
+  double k;
+  long long tile0;
+  int N, L, chunk, nrb, chunks, active;
+};
+
+template <int L, typename R, typename C = Config<L, R>>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    rtr_batch_kernel(const BatchSys* __restrict__ sys, int nsys, long long ntiles,
+                     unsigned long long* __restrict__ counter) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  constexpr int NH = L * (L + 2);
+  __shared__ long long tile_s;
+  for (;;) {
+    if (threadIdx.x == 0) tile_s = static_cast<long long>(atomicAdd(counter, 1ULL));
+    __syncthreads();
+    const long long t = tile_s;
+    __syncthreads();
+    if (t >= ntiles) break;
+    // system holding tile t (tile0 ascending)
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sys[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchSys& S = sys[lo];
+    if (!S.active) continue;
+    const int local = static_cast<int>(t - S.tile0);
+    const int rb = local % S.nrb, ch = local / S.nrb;
+    if (ch >= S.chunks) continue;  // never taken with consistent descriptors
+    const int j0 = ch * S.chunk;
+    const int j1 = min(S.N, j0 + S.chunk);
+    rtr_tile<L, R, C>(S.N, S.pos, static_cast<const Pair2<R>*>(S.x),
+                      static_cast<Pair2<R>*>(S.partial) + (size_t)ch * S.N * (2 * NH), S.k, rb, j0, j1,
+                      smem_raw);
+  }
+}
+
+// one-time setup of a kernel's shared-memory limit; returns its resident CTAs
+// per SM (0 on error)
+template <typename K>
+int kernel_setup(K* kern, int block, size_t smem) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess) return 0;
+  return occ;
+}
+
+// resident CTAs of the per-context kernel on the whole GPU (SMs x CTAs per SM)
+template <int L, typename R, typename C = Config<L, R>>
+int resident_slots() {
+  static const int occ = kernel_setup(rtr_partial_kernel<L, R, C>, C::BLOCK, Layout<L, R, C>::bytes);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * (occ > 0 ? occ : 1);
+}
+
+template <int L, typename R, typename C = Config<L, R>>
 cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
                            cudaStream_t st) {
-  using C = Config<L, R>;
-  using LY = Layout<L, R>;
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(rtr_partial_kernel<L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(LY::bytes));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  using LY = Layout<L, R, C>;
+  static const int occ = kernel_setup(rtr_partial_kernel<L, R, C>, C::BLOCK, LY::bytes);
+  if (occ < 1) return cudaErrorInvalidConfiguration;
   if (N <= 0) return cudaSuccess;
   if (chunks < 1) chunks = 1;
   const int64_t chunk = (N + chunks - 1) / chunks;
   dim3 grid(static_cast<unsigned>((N + C::BLOCK - 1) / C::BLOCK), static_cast<unsigned>(chunks));
-  rtr_partial_kernel<L, R><<<grid, C::BLOCK, LY::bytes, st>>>(static_cast<int>(N), static_cast<const Pos4*>(pos),
+  rtr_partial_kernel<L, R, C><<<grid, C::BLOCK, LY::bytes, st>>>(static_cast<int>(N), static_cast<const Pos4*>(pos),
                                                                static_cast<const Pair2<R>*>(x),
                                                                static_cast<Pair2<R>*>(partial), k,
                                                                static_cast<int>(chunk));
+  note_launch();
+  return cudaGetLastError();
+}
+
+// persistent batched launch: one CTA per resident slot, tiles from `counter`
+// (zeroed by the caller before the launch)
+template <int L, typename R, typename C = Config<L, R>>
+cudaError_t launch_batch(const void* sys, int nsys, long long ntiles, unsigned long long* counter, cudaStream_t st) {
+  using LY = Layout<L, R, C>;
+  static const int occ = kernel_setup(rtr_batch_kernel<L, R, C>, C::BLOCK, LY::bytes);
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (nsys <= 0 || ntiles <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long slots = static_cast<long long>(sms) * occ;
+  const unsigned grid = static_cast<unsigned>(ntiles < slots ? ntiles : slots);
+  rtr_batch_kernel<L, R, C><<<grid, C::BLOCK, LY::bytes, st>>>(static_cast<const BatchSys*>(sys), nsys, ntiles,
+                                                                counter);
   note_launch();
   return cudaGetLastError();
 }
