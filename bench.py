@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-ensemble measurement")
     ap.add_argument("--batched-ensembles", type=int, default=12)
     ap.add_argument("--batched-rhs", type=int, default=4)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess measurement")
     return ap.parse_args()
 
 
@@ -271,6 +272,57 @@ def run_batched(args, local_rank):
             B.celes_destroy(c)
 
 
+def run_learned(args, local_rank):
+    """The graph-network first iterate: trained on solved ensembles of the
+    learned-guess recipe (R = 100 nm, n = 1.52, L = 3, plane wave; N reduced
+    to 800..1600 so the measurement takes seconds), evaluated on a held-out
+    ensemble of 3000 spheres against the T a start (mixed solve to 1e-6)."""
+    import synth
+    from paper_1706_02145_gb300 import binding as B
+    train = []
+    try:
+        t0 = time.perf_counter()
+        for i in range(6):
+            sc = synth.config4(i, N=800 + 160 * i)
+            c = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, device=local_rank)
+            train.append(c)
+            B.celes_set_incident(c, [B.make_incident("plane", beta=0.0, alpha=0.0, pol=2)])
+            B.celes_solve(c, 1e-8, mode=B.CELES_SOLVE_MIXED)
+        t_solve = time.perf_counter() - t0
+        g = B.celes_gnn_create(3, width=128, layers=3, seed=1, device=local_rank)
+        try:
+            t0 = time.perf_counter()
+            first = float(np.mean([B.celes_gnn_train(g, c, steps=0) for c in train]))
+            epochs = 60
+            for _ in range(epochs):
+                for c in train:
+                    B.celes_gnn_train(g, c, steps=1, lr=1e-3)
+            last = float(np.mean([B.celes_gnn_train(g, c, steps=0) for c in train]))
+            t_train = time.perf_counter() - t0
+            ev = synth.config4(1000, N=3000)
+            ce = B.celes_create(ev.positions, ev.radii, ev.n_sphere, ev.n0, ev.k0, ev.lmax, device=local_rank)
+            try:
+                B.celes_set_incident(ce, [B.make_incident("plane", beta=0.0, alpha=0.0, pol=2)])
+                B.celes_solve(ce, TOL, mode=B.CELES_SOLVE_MIXED)  # warm-up
+                base = B.celes_solve(ce, TOL, mode=B.CELES_SOLVE_MIXED)
+                t0 = time.perf_counter()
+                B.celes_gnn_predict(g, ce)
+                t_pred = time.perf_counter() - t0
+                lg = B.celes_solve(ce, TOL, mode=B.CELES_SOLVE_MIXED, x0=B.CELES_X0_LEARNED)
+            finally:
+                B.celes_destroy(ce)
+        finally:
+            B.celes_gnn_destroy(g)
+        return {"train_ensembles": len(train), "train_N": [800 + 160 * i for i in range(6)], "epochs": epochs,
+                "train_solve_s": t_solve, "train_s": t_train, "loss_first": first, "loss_last": last,
+                "eval_N": 3000, "ta_iterations": base["iterations"], "ta_s": base["seconds"],
+                "learned_iterations": lg["iterations"], "learned_s": lg["seconds"], "predict_s": t_pred,
+                "learned_guess_used": lg["guess_used"], "learned_residual": lg["residual"]}
+    finally:
+        for c in train:
+            B.celes_destroy(c)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import synth
@@ -409,6 +461,7 @@ def run_ours(args, rank, world, local_rank):
             B.celes_destroy(cs)
     B.celes_destroy(ctx)
     batched = None if args.no_batched else run_batched(args, local_rank)
+    learned = None if args.no_learned else run_learned(args, local_rank)
 
     # end to end through the C ABI with host buffers: H2D of the inputs,
     # D2H of the coefficients, every step
@@ -459,7 +512,7 @@ def run_ours(args, rank, world, local_rank):
                                        "step = incident coefficients + FP32/FP64-refined GMRES to 1e-6 + far field",
                            "N": N, "lmax": L, "tol": TOL, "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MB write); inputs resident in HBM"},
-                "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "batched": batched,
+                "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "batched": batched, "learned_guess": learned,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

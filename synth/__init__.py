@@ -218,6 +218,27 @@ def config3(index: int, n_rhs: int = 8, N: Optional[int] = None, lmax: Optional[
                  name=f"ensemble {index}: N={N} L={L} lambda={lam:.0f} fill={fill:.2f}")
 
 
+def config4(index: int, N: Optional[int] = None, fill: Optional[float] = None) -> Scene:
+    """Learned-guess ensembles: R = 100 nm, n = 1.52, lambda = 550 nm, L = 3,
+    x-polarised plane wave along +z, random sequential addition in a cube;
+    N ~ U[1000, 5000] and fill ~ U[0.2, 0.35] unless given."""
+    rng = rng_for(4, index)
+    N_ = int(rng.integers(1000, 5001))
+    fill_ = float(rng.uniform(0.2, 0.35))
+    N = N_ if N is None else N
+    fill = fill_ if fill is None else fill
+    R = 100.0
+    side = (N * 4.0 / 3.0 * np.pi * R ** 3 / fill) ** (1.0 / 3.0)
+    radii = np.full(N, R)
+
+    def sampler(rng, r, m):
+        return rng.uniform(r, side - r, size=(m, 3))
+
+    pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side))
+    return Scene(pos, radii, np.full(N, 1.52 + 0j), 1.0, 550.0, 3,
+                 [Incident("plane", beta=0.0, alpha=0.0, pol=2)], name=f"learned-guess cube N={N} fill={fill:.2f}")
+
+
 def config5(seed_index: int = 0, N: int = 100_000) -> Scene:
     rng = rng_for(5, seed_index)
     R = 130.0
