@@ -168,7 +168,7 @@ struct celes_ctx {
   bool has_precond = false;
   int64_t nblocks = 0;
   int max_block_dim = 0;
-  DevBuf block_off, mat_off, perm, mats, piv, info, pwork;
+  DevBuf block_off, mat_off, perm, mats, mats32, piv, pivperm, info, pwork;
   // small device scratch
   DevBuf dots, dot_partial, flag;
   std::string err;
@@ -444,6 +444,8 @@ extern "C" void celes_destroy(celes_ctx* c) {
     c->mat_off.release();
     c->perm.release();
     c->mats.release();
+    c->mats32.release();
+    c->pivperm.release();
     c->piv.release();
     c->info.release();
     c->pwork.release();
@@ -640,6 +642,7 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
   CK(c->mat_off.ensure(sizeof(int64_t) * (nb + 1)), "matrix offsets");
   CK(c->perm.ensure(sizeof(int) * c->N), "perm");
   CK(c->mats.ensure(sizeof(double) * 2 * moff[nb]), "LU factors");
+  CK(c->mats32.ensure(sizeof(float) * 2 * moff[nb]), "LU factors (FP32 copy)");
   CK(c->piv.ensure(sizeof(int) * c->N * c->nmax), "pivots");
   CK(c->info.ensure(sizeof(int) * nb), "info");
   CK(cudaMemcpyAsync(c->block_off.p, boff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, c->stream), "h2d");
@@ -651,6 +654,10 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
   CK(launch_precond_lu(nb, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax, c->mats.as<double>(),
                        c->piv.as<int>(), c->info.as<int>(), c->stream),
      "precond LU");
+  CK(launch_f64_to_f32(2 * moff[nb], c->mats.as<double>(), c->mats32.as<float>(), c->stream), "FP32 factors");
+  CK(c->pivperm.ensure(sizeof(int) * c->N * c->nmax), "pivot permutation");
+  CK(launch_pivot_perm(nb, c->block_off.as<int64_t>(), c->nmax, c->piv.as<int>(), c->pivperm.as<int>(), c->stream),
+     "pivot permutation");
   std::vector<int> hinfo(nb);
   CK(cudaMemcpyAsync(hinfo.data(), c->info.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream), "d2h");
   CK(cudaStreamSynchronize(c->stream), "sync");
@@ -666,13 +673,13 @@ static int precond_apply_internal(celes_ctx* c, const void* x, void* y, int nrhs
   CK(c->pwork.ensure(sizeof(double) * 2 * c->N * c->nmax * nrhs), "precond work");
   if (precision == CELES_FP64)
     CK(launch_precond_apply<double>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
-                                    c->perm.as<int>(), c->mats.as<double>(), c->piv.as<int>(), c->N, nrhs, x, y,
-                                    c->pwork.as<double>(), c->max_block_dim, st),
+                                    c->perm.as<int>(), c->mats.as<double>(), c->mats32.as<float>(), c->pivperm.as<int>(),
+                                    c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st),
        "precond apply");
   else
     CK(launch_precond_apply<float>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
-                                   c->perm.as<int>(), c->mats.as<double>(), c->piv.as<int>(), c->N, nrhs, x, y,
-                                   c->pwork.as<double>(), c->max_block_dim, st),
+                                   c->perm.as<int>(), c->mats.as<double>(), c->mats32.as<float>(), c->pivperm.as<int>(),
+                                   c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st),
        "precond apply");
   return CELES_OK;
 }

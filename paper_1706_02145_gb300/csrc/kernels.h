@@ -95,7 +95,12 @@ cudaError_t launch_precond_lu(int64_t nblocks, const int64_t* block_off, const i
                               double* mats, int* piv, int* info, cudaStream_t st);
 template <typename R>
 cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
-                                 const int* perm, const double* mats, const int* piv, int64_t N, int nrhs,
-                                 const void* x, void* y, double* work, int max_block_dim, cudaStream_t st);
+                                 const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
+                                 int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st);
+// per block, the gather permutation equivalent to the LU's row interchanges
+cudaError_t launch_pivot_perm(int64_t nblocks, const int64_t* block_off, int nmax, const int* piv, int* pivperm,
+                              cudaStream_t st);
+// elementwise FP64 -> FP32
+cudaError_t launch_f64_to_f32(int64_t n, const double* a, float* b, cudaStream_t st);
 
 }  // namespace celes

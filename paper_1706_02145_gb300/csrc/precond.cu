@@ -122,100 +122,217 @@ cudaError_t launch_precond_lu(int64_t nblocks, const int64_t* block_off, const i
 
 // ---------------------------------------------------------------------------
 // apply: one CTA per (block, rhs): gather, permute, forward and back
-// substitution in FP64, scatter
+// substitution, scatter.  The block's vector lives in shared memory when it
+// fits (one barrier per substitution step), else in the global work array.
+// Factors in the precision F: FP64, or an FP32 copy for FP32 vectors (a
+// preconditioner only has to be the same operator wherever it is applied).
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename F>
+__device__ __forceinline__ Pair2<F> cmul_sub(Pair2<F> a, Pair2<F> l, Pair2<F> y) {
+  return Pair2<F>{a.re - (l.re * y.re - l.im * y.im), a.im - (l.re * y.im + l.im * y.re)};
+}
+
+// acc - sum_{j < tb} A[i, kb + j] v[kb + j]; a full 32-column tile is
+// unrolled so that a thread's 32 factor loads are all in flight at once
+template <typename F>
+__device__ __forceinline__ Pair2<F> tile_gemv(const Pair2<F>* __restrict__ A, int64_t n, int64_t i, int64_t kb,
+                                              int tb, const Pair2<F>* v, Pair2<F> acc) {
+  const Pair2<F>* col = A + i + kb * n;
+  if (tb == 32) {
+    Pair2<F> a[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = col[j * n];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc = cmul_sub(acc, a[j], v[kb + j]);
+  } else {
+    for (int j = 0; j < tb; ++j) acc = cmul_sub(acc, col[j * n], v[kb + j]);
+  }
+  return acc;
+}
+
+template <typename F>
+__device__ __forceinline__ Pair2<F> shfl_pair(Pair2<F> v, int src) {
+  return Pair2<F>{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+
+// Blocked substitution: warp 0 resolves each 32-row diagonal tile with
+// shuffles (no block barrier inside a tile), then the whole CTA applies the
+// tile's columns to the remaining rows (a GEMV over contiguous column
+// segments).  Two barriers per 32 unknowns instead of one or two per unknown.
+// The row permutation of partial pivoting is folded into the gather (pivperm:
+// position i of the permuted vector holds original entry pivperm[i]).
+template <typename R, typename F, bool SMEM>
 __global__ void __launch_bounds__(256) precond_apply_kernel(const int64_t* __restrict__ block_off,
                                                             const int64_t* __restrict__ mat_off, int nmax,
                                                             const int* __restrict__ perm,
-                                                            const double2* __restrict__ mats,
-                                                            const int* __restrict__ piv, int64_t N,
+                                                            const Pair2<F>* __restrict__ mats,
+                                                            const int* __restrict__ pivperm, int64_t N,
                                                             const Pair2<R>* __restrict__ x, Pair2<R>* __restrict__ y,
-                                                            double2* __restrict__ work) {
+                                                            Pair2<F>* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char pa_smem[];
   const int64_t q = blockIdx.x;
   const int rhs = blockIdx.y;
   const int64_t s0 = block_off[q];
   const int64_t ns = block_off[q + 1] - s0;
   const int64_t n = ns * nmax;
-  const double2* A = mats + mat_off[q];
-  const int* pv = piv + s0 * nmax;
-  double2* v = work + (int64_t)rhs * N * nmax + s0 * nmax;
+  const Pair2<F>* A = mats + mat_off[q];
+  const int* pp = pivperm + s0 * nmax;
+  Pair2<F>* v = SMEM ? reinterpret_cast<Pair2<F>*>(pa_smem) : work + (int64_t)rhs * N * nmax + s0 * nmax;
   const Pair2<R>* xr = x + (int64_t)rhs * N * nmax;
   Pair2<R>* yr = y + (int64_t)rhs * N * nmax;
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const int64_t src = pp[t];
+    const int64_t a = src / nmax;
+    const int r = static_cast<int>(src - a * nmax);
+    const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
+    v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
+  }
+  __syncthreads();
+  // the diagonal tile is staged in shared memory by the whole CTA (one
+  // memory latency) before warp 0 walks its 32 dependent steps
+  __shared__ Pair2<F> dt[32][33];
+  auto stage = [&](int64_t kb, int tb) {
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+      const int j = t >> 5, i = t & 31;  // column j, row i: coalesced along i
+      dt[j][i] = (i < tb && j < tb) ? A[(kb + i) + (kb + j) * n] : Pair2<F>{0, 0};
+    }
+  };
+  // forward substitution with the unit lower factor
+  for (int64_t kb = 0; kb < n; kb += 32) {
+    const int tb = static_cast<int>(n - kb < 32 ? n - kb : 32);
+    stage(kb, tb);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      Pair2<F> yl = lane < tb ? v[kb + lane] : Pair2<F>{0, 0};
+      for (int j = 0; j < tb; ++j) {
+        const Pair2<F> yj = shfl_pair(yl, j);
+        if (lane > j && lane < tb) yl = cmul_sub(yl, dt[j][lane], yj);
+      }
+      if (lane < tb) v[kb + lane] = yl;
+    }
+    __syncthreads();
+    for (int64_t i = kb + tb + threadIdx.x; i < n; i += blockDim.x) v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+    __syncthreads();
+  }
+  // back substitution with the upper factor (tiles from the bottom)
+  const int64_t ntile = (n + 31) / 32;
+  for (int64_t tt = ntile - 1; tt >= 0; --tt) {
+    const int64_t kb = tt * 32;
+    const int tb = static_cast<int>(n - kb < 32 ? n - kb : 32);
+    stage(kb, tb);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      Pair2<F> yl = lane < tb ? v[kb + lane] : Pair2<F>{0, 0};
+      for (int j = tb - 1; j >= 0; --j) {
+        if (lane == j) {
+          const Pair2<F> u = dt[j][j];
+          const F den = u.re * u.re + u.im * u.im;
+          yl = Pair2<F>{(yl.re * u.re + yl.im * u.im) / den, (yl.im * u.re - yl.re * u.im) / den};
+        }
+        const Pair2<F> xj = shfl_pair(yl, j);
+        if (lane < j) yl = cmul_sub(yl, dt[j][lane], xj);
+      }
+      if (lane < tb) v[kb + lane] = yl;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < kb; i += blockDim.x) v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+    __syncthreads();
+  }
   for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
     const int64_t a = t / nmax;
     const int r = static_cast<int>(t - a * nmax);
-    const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
-    v[t] = make_double2(static_cast<double>(e.re), static_cast<double>(e.im));
+    yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
   }
+}
+
+// position -> source index of the row interchanges of each block's LU
+// (applied in order kk = 0..n-1, as the factorisation recorded them)
+__global__ void pivot_perm_kernel(const int64_t* __restrict__ block_off, int nmax, const int* __restrict__ piv,
+                                  int* __restrict__ pivperm) {
+  const int64_t q = blockIdx.x;
+  const int64_t s0 = block_off[q];
+  const int64_t n = (block_off[q + 1] - s0) * nmax;
+  const int* pv = piv + s0 * nmax;
+  int* pp = pivperm + s0 * nmax;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) pp[t] = static_cast<int>(t);
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int64_t kk = 0; kk < n; ++kk) {
       const int64_t p = pv[kk];
       if (p != kk) {
-        const double2 t = v[kk];
-        v[kk] = v[p];
-        v[p] = t;
+        const int t = pp[kk];
+        pp[kk] = pp[p];
+        pp[p] = t;
       }
     }
   }
-  __syncthreads();
-  // forward substitution with the unit lower factor (column oriented)
-  for (int64_t kk = 0; kk < n; ++kk) {
-    const double2 yk = v[kk];
-    for (int64_t i = kk + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double2 l = A[i + kk * n];
-      double2 a = v[i];
-      a.x -= l.x * yk.x - l.y * yk.y;
-      a.y -= l.x * yk.y + l.y * yk.x;
-      v[i] = a;
-    }
-    __syncthreads();
-  }
-  // back substitution with the upper factor
-  for (int64_t kk = n - 1; kk >= 0; --kk) {
-    if (threadIdx.x == 0) {
-      const double2 u = A[kk + kk * n];
-      const cd z = mkc(v[kk].x, v[kk].y) / mkc(u.x, u.y);
-      v[kk] = make_double2(z.re, z.im);
-    }
-    __syncthreads();
-    const double2 xk = v[kk];
-    for (int64_t i = threadIdx.x; i < kk; i += blockDim.x) {
-      const double2 u = A[i + kk * n];
-      double2 a = v[i];
-      a.x -= u.x * xk.x - u.y * xk.y;
-      a.y -= u.x * xk.y + u.y * xk.x;
-      v[i] = a;
-    }
-    __syncthreads();
-  }
-  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-    const int64_t a = t / nmax;
-    const int r = static_cast<int>(t - a * nmax);
-    yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(v[t].x), static_cast<R>(v[t].y)};
-  }
 }
 
-template <typename R>
-cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
-                                 const int* perm, const double* mats, const int* piv, int64_t N, int nrhs,
-                                 const void* x, void* y, double* work, int max_block_dim, cudaStream_t st) {
-  (void)max_block_dim;
+cudaError_t launch_pivot_perm(int64_t nblocks, const int64_t* block_off, int nmax, const int* piv, int* pivperm,
+                              cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(nblocks), static_cast<unsigned>(nrhs));
-  precond_apply_kernel<R><<<grid, 256, 0, st>>>(block_off, mat_off, nmax, perm,
-                                                reinterpret_cast<const double2*>(mats), piv, N,
-                                                static_cast<const Pair2<R>*>(x), static_cast<Pair2<R>*>(y),
-                                                reinterpret_cast<double2*>(work));
+  pivot_perm_kernel<<<static_cast<unsigned>(nblocks), 256, 0, st>>>(block_off, nmax, piv, pivperm);
   note_launch();
   return cudaGetLastError();
 }
+
+template <typename R, typename F>
+cudaError_t launch_apply_t(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
+                           const int* perm, const void* mats, const int* piv, int64_t N, int nrhs, const void* x,
+                           void* y, void* work, int max_block_dim, cudaStream_t st) {
+  dim3 grid(static_cast<unsigned>(nblocks), static_cast<unsigned>(nrhs));
+  const size_t smem = sizeof(Pair2<F>) * static_cast<size_t>(max_block_dim);
+  if (smem <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      const cudaError_t e = cudaFuncSetAttribute(precond_apply_kernel<R, F, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    precond_apply_kernel<R, F, true><<<grid, 256, smem, st>>>(
+        block_off, mat_off, nmax, perm, static_cast<const Pair2<F>*>(mats), piv, N, static_cast<const Pair2<R>*>(x),
+        static_cast<Pair2<R>*>(y), static_cast<Pair2<F>*>(work));
+  } else {
+    precond_apply_kernel<R, F, false><<<grid, 256, 0, st>>>(
+        block_off, mat_off, nmax, perm, static_cast<const Pair2<F>*>(mats), piv, N, static_cast<const Pair2<R>*>(x),
+        static_cast<Pair2<R>*>(y), static_cast<Pair2<F>*>(work));
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// FP64 vectors use the FP64 factors; FP32 vectors the FP32 copy (mats32)
+template <typename R>
+cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
+                                 const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
+                                 int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  if constexpr (sizeof(R) == 8)
+    return launch_apply_t<double, double>(nblocks, block_off, mat_off, nmax, perm, mats, piv, N, nrhs, x, y, work,
+                                          max_block_dim, st);
+  else
+    return launch_apply_t<float, float>(nblocks, block_off, mat_off, nmax, perm, mats32, piv, N, nrhs, x, y, work,
+                                        max_block_dim, st);
+}
 template cudaError_t launch_precond_apply<float>(int64_t, const int64_t*, const int64_t*, int, const int*,
-                                                 const double*, const int*, int64_t, int, const void*, void*, double*,
-                                                 int, cudaStream_t);
+                                                 const double*, const float*, const int*, int64_t, int, const void*,
+                                                 void*, double*, int, cudaStream_t);
 template cudaError_t launch_precond_apply<double>(int64_t, const int64_t*, const int64_t*, int, const int*,
-                                                  const double*, const int*, int64_t, int, const void*, void*,
-                                                  double*, int, cudaStream_t);
+                                                  const double*, const float*, const int*, int64_t, int, const void*,
+                                                  void*, double*, int, cudaStream_t);
+
+__global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = static_cast<float>(a[t]);
+}
+cudaError_t launch_f64_to_f32(int64_t n, const double* a, float* b, cudaStream_t st) {
+  const int64_t blocks = (n + 255) / 256;
+  f64_to_f32_kernel<<<static_cast<unsigned>(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16), 256, 0, st>>>(
+      n, a, b);
+  note_launch();
+  return cudaGetLastError();
+}
 
 }  // namespace celes
