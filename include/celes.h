@@ -209,6 +209,14 @@ int celes_nearfield(celes_ctx* ctx, const double* points, int64_t Np, int rhs, i
  * quadrature error. */
 int celes_power(celes_ctx* ctx, int rhs, int n_beta, int n_alpha, double* R, double* T);
 
+/* Phase-matrix element S11 (Sec. 4: the average of a TE and a TM run's
+ * far-field intensity): s11[i] = (1/2) sum over the two RHS rhs_a, rhs_b of
+ * the azimuthal mean (n_alpha trapezoid nodes) of sum_j |g_j(alpha, beta_i)|^2
+ * (App. D), for n_beta polar angles betas (host); unnormalised (divide by the
+ * forward value for S11(0) = 1).  Needs a solution.  Errors: EINVAL, ESTATE,
+ * ENOMEM, ECUDA. */
+int celes_s11(celes_ctx* ctx, int rhs_a, int rhs_b, const double* betas, int n_beta, int n_alpha, double* s11);
+
 /* Problem sizes. */
 int64_t celes_num_spheres(const celes_ctx* ctx);
 int celes_nmax(const celes_ctx* ctx);

@@ -52,3 +52,18 @@ def c_sca_quadrature(lmax, k, positions, b, n_beta=64, n_alpha=128, E0=1.0):
     I = np.sum(np.abs(g) ** 2, axis=1).reshape(n_beta, n_alpha)
     total = np.sum(wg[:, None] * I) * (2.0 * np.pi / n_alpha)
     return float(4.0 * np.pi ** 2 / k ** 2 * total / abs(E0) ** 2)
+
+
+def s11_azimuthal(lmax, k, positions, b_te, b_tm, betas, n_alpha=64):
+    """S11(beta) as in the phase-matrix comparison of Sec. 4: the scattered
+    intensity sum_j |g_j|^2 averaged over the azimuth (trapezoid, n_alpha
+    nodes) and over a TE and a TM run, unnormalised."""
+    betas = np.atleast_1d(np.asarray(betas, dtype=float))
+    alpha = 2.0 * np.pi * np.arange(n_alpha) / n_alpha
+    B, A = np.meshgrid(betas, alpha, indexing="ij")
+    dirs = np.stack([B.ravel(), A.ravel()], axis=1)
+    out = np.zeros(betas.size)
+    for b in (b_te, b_tm):
+        g = farfield_amplitude(lmax, k, positions, b, dirs)
+        out += np.sum(np.abs(g) ** 2, axis=1).reshape(betas.size, n_alpha).mean(axis=1)
+    return 0.5 * out

@@ -127,6 +127,7 @@ SIGNATURES = [
                                          ctypes.POINTER(celes_solve_info)]),
     ("celes_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("celes_batch_destroy", None, [ctypes.c_void_p]),
+    ("celes_s11", ctypes.c_int, [_c_ctx_p, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp]),
     ("celes_power", ctypes.c_int, [_c_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     ("celes_nearfield", ctypes.c_int, [_c_ctx_p, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp]),
     ("celes_destroy", None, [_c_ctx_p]),
@@ -417,6 +418,14 @@ def celes_nearfield(ctx, points, rhs=0, what=2):
     E = np.zeros((p.shape[0], 3), dtype=np.complex128)
     _check(load().celes_nearfield(ctx, _dptr(p), p.shape[0], int(rhs), int(what), _dptr(E.view(np.float64))), ctx)
     return E
+
+
+def celes_s11(ctx, betas, rhs_a=0, rhs_b=1, n_alpha=64):
+    """Unnormalised S11 at polar angles betas (TE/TM average of the azimuthally averaged far-field intensity)."""
+    b = np.ascontiguousarray(betas, dtype=np.float64).ravel()
+    out = np.zeros(b.size)
+    _check(load().celes_s11(ctx, int(rhs_a), int(rhs_b), _dptr(b), b.size, int(n_alpha), _dptr(out)), ctx)
+    return out
 
 
 def celes_power(ctx, rhs=0, n_beta=128, n_alpha=128):

@@ -151,3 +151,80 @@ extern "C" int celes_power(celes_ctx* ctx, int rhs, int n_beta, int n_alpha, dou
   *R = pb / pin;
   return CELES_OK;
 }
+
+namespace celes {
+namespace {
+// s11[ib] = (1 / (2 n_alpha)) sum_alpha sum_j (|g_a,j|^2 + |g_b,j|^2), one block per beta
+__global__ void s11_kernel(int n_alpha, const double* __restrict__ ga, const double* __restrict__ gb,
+                           double* __restrict__ s11) {
+  __shared__ double red[kPowThreads];
+  const int64_t base = (int64_t)blockIdx.x * n_alpha;
+  double s = 0.0;
+  for (int ia = threadIdx.x; ia < n_alpha; ia += blockDim.x) {
+    const double* p = ga + 4 * (base + ia);
+    const double* q = gb + 4 * (base + ia);
+    s += p[0] * p[0] + p[1] * p[1] + p[2] * p[2] + p[3] * p[3] + q[0] * q[0] + q[1] * q[1] + q[2] * q[2] +
+         q[3] * q[3];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kPowThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s11[blockIdx.x] = red[0] / (2.0 * n_alpha);
+}
+}  // namespace
+}  // namespace celes
+
+extern "C" int celes_s11(celes_ctx* ctx, int rhs_a, int rhs_b, const double* betas, int n_beta, int n_alpha,
+                         double* s11) {
+  using namespace celes;
+  if (!ctx || !betas || !s11 || n_beta < 1 || n_alpha < 1 || n_alpha > 1 << 20) return CELES_EINVAL;
+  CtxView v{};
+  int s = ctx_view(ctx, &v);
+  if (s) return s;
+  if (rhs_a < 0 || rhs_a >= v.nrhs || rhs_b < 0 || rhs_b >= v.nrhs) return CELES_EINVAL;
+  if (!v.has_b) return CELES_ESTATE;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(v.device);
+  struct Restore {
+    int d;
+    ~Restore() { cudaSetDevice(d); }
+  } restore{prev};
+  const int64_t Nd = (int64_t)n_beta * n_alpha;
+  std::vector<double> dirs(2 * Nd);
+  for (int ib = 0; ib < n_beta; ++ib)
+    for (int ia = 0; ia < n_alpha; ++ia) {
+      dirs[2 * ((int64_t)ib * n_alpha + ia)] = betas[ib];
+      dirs[2 * ((int64_t)ib * n_alpha + ia) + 1] = 2.0 * M_PI * ia / n_alpha;
+    }
+  const cudaStream_t st = v.stream;
+  double *dd = nullptr, *ga = nullptr, *gb = nullptr, *ds = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    if (dd) cudaFree(dd);
+    if (ga) cudaFree(ga);
+    if (gb) cudaFree(gb);
+    if (ds) cudaFree(ds);
+  };
+  if (cudaMalloc(&dd, sizeof(double) * 2 * Nd) != cudaSuccess || cudaMalloc(&ga, sizeof(double) * 4 * Nd) != cudaSuccess ||
+      cudaMalloc(&gb, sizeof(double) * 4 * Nd) != cudaSuccess || cudaMalloc(&ds, sizeof(double) * n_beta) != cudaSuccess) {
+    cleanup();
+    return CELES_ENOMEM;
+  }
+  const size_t per = (size_t)v.N * v.nmax * 2;
+  cudaError_t e = cudaMemcpyAsync(dd, dirs.data(), sizeof(double) * 2 * Nd, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_farfield(v.N, v.L, v.k, v.pos, v.b + per * rhs_a, Nd, dd, ga, st);
+  if (e == cudaSuccess) e = launch_farfield(v.N, v.L, v.k, v.pos, v.b + per * rhs_b, Nd, dd, gb, st);
+  if (e == cudaSuccess) {
+    s11_kernel<<<n_beta, kPowThreads, 0, st>>>(n_alpha, ga, gb, ds);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s11, ds, sizeof(double) * n_beta, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  return e == cudaSuccess ? CELES_OK : CELES_ECUDA;
+}

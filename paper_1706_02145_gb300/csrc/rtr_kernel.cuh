@@ -100,9 +100,41 @@ __device__ __forceinline__ void geometry_angles(float ct, float st, float cph, f
   geometry_angles_t<L, float>(ct, st, cph, sph, g);
 }
 
+// the few scalars every table of a pair derives from
+struct GeomS {
+  float ix, sn, cs;        // 1/(k d), sin(k d), cos(k d)
+  float ct, st, cph, sph;  // cos/sin theta, cos/sin phi of d
+};
+
+// h_p(k d), p = 0..2L (closed forms of h_0, h_1 and upward recurrence)
+template <int L>
+__device__ __forceinline__ void fill_hankel(const GeomS& q, Geom<L, float>& g) {
+  constexpr int PM = 2 * L;
+  const float ix = q.ix, sn = q.sn, cs = q.cs;
+  g.hre[0] = sn * ix;
+  g.him[0] = -cs * ix;
+  g.hre[1] = -ix * fma_(-sn, ix, cs);
+  g.him[1] = -ix * fma_(cs, ix, sn);
+#pragma unroll
+  for (int p = 1; p < PM; ++p) {
+    const float c = static_cast<float>(2 * p + 1) * ix;
+    g.hre[p + 1] = fma_(c, g.hre[p], -g.hre[p - 1]);
+    g.him[p + 1] = fma_(c, g.him[p], -g.him[p - 1]);
+  }
+}
+
+template <int L>
+__device__ __forceinline__ GeomS geometry_ff_scalars(const PosFF& a, const PosFF& b);
+
 template <int L>
 __device__ __forceinline__ void geometry_ff(const PosFF& a, const PosFF& b, Geom<L, float>& g) {
-  constexpr int PM = 2 * L;
+  const GeomS q = geometry_ff_scalars<L>(a, b);
+  fill_hankel<L>(q, g);
+  geometry_angles<L>(q.ct, q.st, q.cph, q.sph, g);
+}
+
+template <int L>
+__device__ __forceinline__ GeomS geometry_ff_scalars(const PosFF& a, const PosFF& b) {
   // k (r_a - r_b) per axis as s + e (unnormalised; |e| << |s| or s == 0)
   float sx, ex, sy, ey, sz, ez;
   two_diff(a.xh, b.xh, sx, ex);
@@ -138,25 +170,18 @@ __device__ __forceinline__ void geometry_ff(const PosFF& a, const PosFF& b, Geom
   float sn, cs;
   sincos_quadrant(y, static_cast<int>(n) & 3, sn, cs);
   const float kd = __fadd_rn(r, delta);
-  const float ix = 1.0f / kd;
-  g.hre[0] = sn * ix;
-  g.him[0] = -cs * ix;
-  g.hre[1] = -ix * fma_(-sn, ix, cs);
-  g.him[1] = -ix * fma_(cs, ix, sn);
-#pragma unroll
-  for (int p = 1; p < PM; ++p) {
-    const float c = static_cast<float>(2 * p + 1) * ix;
-    g.hre[p + 1] = fma_(c, g.hre[p], -g.hre[p - 1]);
-    g.him[p + 1] = fma_(c, g.him[p], -g.him[p - 1]);
-  }
+  GeomS q;
+  q.ix = 1.0f / kd;
+  q.sn = sn;
+  q.cs = cs;
   const float dxf = __fadd_rn(sx, ex), dyf = __fadd_rn(sy, ey), dzf = __fadd_rn(sz, ez);
   const float rho = sqrtf(fma_(dxf, dxf, dyf * dyf));
-  const float ct = fminf(1.0f, fmaxf(-1.0f, dzf * rinv));
-  const float st = fminf(1.0f, rho * rinv);
+  q.ct = fminf(1.0f, fmaxf(-1.0f, dzf * rinv));
+  q.st = fminf(1.0f, rho * rinv);
   const float ir = rho > 0.0f ? 1.0f / rho : 0.0f;
-  const float cph = rho > 0.0f ? dxf * ir : 1.0f;
-  const float sph = dyf * ir;
-  geometry_angles<L>(ct, st, cph, sph, g);
+  q.cph = rho > 0.0f ? dxf * ir : 1.0f;
+  q.sph = dyf * ir;
+  return q;
 }
 
 // FP64 pair geometry (the FP64 kernel)
@@ -579,8 +604,35 @@ __device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __rest
   rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
 }
 
+// One pair with the tables rebuilt per stage from the pair's scalars: the
+// half-angle powers and e^{i m phi} for each rotation, h_p for the axial
+// step.  The rebuild before the backward rotation reads the scalars through
+// an optimizer barrier, so the compiler cannot keep the forward rotation's
+// tables alive across the axial step (fewer live registers per thread).
+template <int L, bool INPLACE, bool SYM, typename XV, typename YV, typename Acc>
+__device__ __forceinline__ void pair_lazy(const GeomS& q, const Pair2<float>* __restrict__ xs, XV& xp, YV& yp,
+                                          Acc& acc) {
+  {
+    Geom<L, float> g;
+    geometry_angles<L>(q.ct, q.st, q.cph, q.sph, g);
+    rot_fwd<L>(g, xs, xp, std::make_integer_sequence<int, L>{});
+  }
+  {
+    Geom<L, float> g;
+    fill_hankel<L>(q, g);
+    axial<L, INPLACE, SYM>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
+  }
+  float ct = q.ct, st = q.st, cph = q.cph, sph = q.sph;
+  asm volatile("" : "+f"(ct), "+f"(st), "+f"(cph), "+f"(sph));
+  {
+    Geom<L, float> g;
+    geometry_angles<L>(ct, st, cph, sph, g);
+    rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
+  }
+}
+
 // Launch shape per (lmax, precision), chosen by timing sweeps on GB300 at
-// N = 10 000 (FP32: lmax 3 0.95x, lmax 5 0.31x the time of the earlier shapes)
+// N = 10 000
 template <int L, typename R>
 struct Config {
   static constexpr bool FP64 = sizeof(R) == 8;
@@ -590,6 +642,10 @@ struct Config {
   static constexpr bool XY_SMEM = FP64 && L >= 3;
   static constexpr bool XY_INPLACE = XY_SMEM;  // y' overwrites x' (one shared-memory array)
   static constexpr bool SYM_AXIAL = true;       // axial entries formed once per (l, l') pair
+  // FP32: per-stage geometry tables (pair_lazy); removes the spills at lmax 5
+  // (22.8 vs 26.1 ms); at lmax 4 the full tables are faster (12.3 vs 12.8 ms),
+  // at lmax 3 the two are within run-to-run noise
+  static constexpr bool LAZY_GEOM = !FP64 && L == 5;
   static constexpr int MINB = (!FP64 && L == 3) ? 3 : 1;  // minimum resident CTAs per SM for the allocator
 };
 
@@ -658,8 +714,12 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
     if (active) {
       for (int jj = 0; jj < nj; ++jj) {
         if (jt + jj == i) continue;  // no self coupling
+        constexpr bool LAZY = FF && C::LAZY_GEOM;
         Geom<L, R> g;
-        if constexpr (FF) {
+        GeomS gs;
+        if constexpr (LAZY) {
+          gs = geometry_ff_scalars<L>(rf, sposf[jj]);
+        } else if constexpr (FF) {
           geometry_ff<L>(rf, sposf[jj], g);
         } else {
           const Pos4 rj = spos[jj];
@@ -670,10 +730,12 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
           constexpr bool INPL = C::XY_SMEM && C::XY_INPLACE;
           if constexpr (C::ACC_SMEM) {
             RowAccSmem<R, BLOCK> acc{sacc4 + tid};
-            pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
+            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL>(gs, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
           } else {
             RowAccReg<R> acc{areg};
-            pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
+            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL>(gs, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
           }
         };
         if constexpr (C::XY_SMEM) {

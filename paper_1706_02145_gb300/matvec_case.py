@@ -3,8 +3,9 @@
   python -m paper_1706_02145_gb300.matvec_case --N 6000 --lmax 4 --precision fp32 --kernel rtr --reps 2
 
 Builds the packing of the bench workload's recipe (lognormal radii, cylinder
-slab at fill 0.3) with N spheres and the given lmax, runs `reps` coupling
-matvecs through the C ABI and prints the time of the last one.
+slab at fill 0.3) with N spheres and the given lmax, or the 100 000-sphere
+slab (`--recipe large`), runs `reps` coupling matvecs through the C ABI and
+prints the time of the last one.
 """
 
 import argparse
@@ -24,6 +25,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--kernel", choices=["auto", "direct", "rtr"], default="auto")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--recipe", choices=["slab", "large"], default="slab",
+                    help="slab: the bench recipe (Gaussian-beam cylinder slab) with N spheres and lmax; "
+                         "large: the 100 000-sphere monodisperse slab (lmax 3, N and lmax ignored)")
     a = ap.parse_args()
     import torch
     import synth
@@ -31,7 +35,7 @@ def main():
     B.load()
     kern = {"auto": B.CELES_KERNEL_AUTO, "direct": B.CELES_KERNEL_DIRECT, "rtr": B.CELES_KERNEL_RTR}[a.kernel]
     prec = B.CELES_FP32 if a.precision == "fp32" else B.CELES_FP64
-    sc = synth.config2(0, N=a.N, lmax=a.lmax)
+    sc = synth.config2(0, N=a.N, lmax=a.lmax) if a.recipe == "slab" else synth.config5(0)
     ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, kernel=kern)
     dt = torch.complex64 if prec == B.CELES_FP32 else torch.complex128
     g = torch.Generator(device="cuda").manual_seed(0)

@@ -54,3 +54,19 @@ def test_power_needs_a_gaussian_beam():
             B.celes_power(ctx)
     finally:
         B.celes_destroy(ctx)
+
+
+def test_s11_matches_oracle():
+    from oracle import farfield
+    sc = synth.random_cluster(73, 5, 10, 3, radius=110.0, fill=0.15, n=1.5 + 0.01j)
+    ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, 3)
+    try:
+        B.celes_set_incident(ctx, [B.make_incident("plane", pol=1), B.make_incident("plane", pol=2)])
+        B.celes_solve(ctx, 1e-12, mode=B.CELES_SOLVE_FP64)
+        b = B.celes_get_coefficients(ctx)
+        betas = np.linspace(0.0, np.pi, 19)
+        got = B.celes_s11(ctx, betas, 0, 1, n_alpha=24)
+        ref = farfield.s11_azimuthal(3, sc.k, sc.positions, b[0], b[1], betas, n_alpha=24)
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-10
+    finally:
+        B.celes_destroy(ctx)
