@@ -646,6 +646,7 @@ struct Config {
   // (22.8 vs 26.1 ms); at lmax 4 the full tables are faster (12.3 vs 12.8 ms),
   // at lmax 3 the two are within run-to-run noise
   static constexpr bool LAZY_GEOM = !FP64 && L == 5;
+  static constexpr bool SYNC_PAIR = false;  // barrier per source (keeps a CTA's warps in step)
   static constexpr int MINB = (!FP64 && L == 3) ? 3 : 1;  // minimum resident CTAs per SM for the allocator
 };
 
@@ -711,9 +712,12 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
       for (int q = tid; q < nj; q += BLOCK) spos[q] = pos[jt + q];
     }
     __syncthreads();
-    if (active) {
+    {
       for (int jj = 0; jj < nj; ++jj) {
-        if (jt + jj == i) continue;  // no self coupling
+        // optional barrier per pair: keeps the warps of a CTA on the same
+        // stretch of the (long, fully unrolled) pair code
+        if constexpr (C::SYNC_PAIR) __syncthreads();
+        if (!active || jt + jj == i) continue;  // no self coupling
         constexpr bool LAZY = FF && C::LAZY_GEOM;
         Geom<L, R> g;
         GeomS gs;

@@ -1,0 +1,90 @@
+"""Edge cases of the batched, BiCGSTAB, near-field, power and S11 entry
+points: single spheres (no coupling: b = T a), a batch mixing a one-sphere
+ensemble with larger ones, empty point lists, out-of-range RHS indices."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import incident, mie, solve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1706_02145_gb300 import binding as B  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    B.load()
+
+
+def _ctx(seed, N, L, planes=((0.0, 0.0, 2),)):
+    sc = synth.random_cluster(79, seed, N, L, radius=100.0, fill=0.15, n=1.5 + 0.01j)
+    c = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, L)
+    B.celes_set_incident(c, [B.make_incident("plane", beta=b, alpha=a, pol=p) for (b, a, p) in planes])
+    return sc, c
+
+
+def test_batch_with_a_single_sphere_ensemble():
+    ens = [_ctx(0, 1, 3), _ctx(1, 2, 2), _ctx(2, 30, 3, ((0.0, 0.0, 2), (0.5, 1.0, 1)))]
+    try:
+        bt = B.celes_batch_create([c for _, c in ens])
+        try:
+            code, infos = B.celes_batch_solve(bt, len(ens), 1e-10, mode=B.CELES_SOLVE_FP64)
+            assert code == B.CELES_OK and all(i["residual"] <= 1e-10 for i in infos)
+        finally:
+            B.celes_batch_destroy(bt)
+        for sc, c in ens:
+            t = mie.t_diagonal(sc.lmax, sc.k, sc.radii, sc.n_rel)
+            got = B.celes_get_coefficients(c)
+            planes = ((0.0, 0.0, 2), (0.5, 1.0, 1))
+            for r in range(B.celes_num_rhs(c)):
+                b, a, p = planes[r]
+                ain = incident.plane_wave_coeffs(sc.lmax, sc.k, sc.positions, b, a, p)
+                ref = solve.solve_dense(sc.positions, sc.k, sc.lmax, t, ain)
+                assert rel(got[r], ref) <= 1e-8
+        # one sphere: no coupling at all, b = T a exactly
+        sc0, c0 = ens[0]
+        t0 = mie.t_diagonal(3, sc0.k, sc0.radii, sc0.n_rel)
+        a0 = incident.plane_wave_coeffs(3, sc0.k, sc0.positions, 0.0, 0.0, 2)
+        assert rel(B.celes_get_coefficients(c0)[0], t0 * a0) <= 1e-12
+    finally:
+        for _, c in ens:
+            B.celes_destroy(c)
+
+
+def test_bicgstab_single_sphere_and_tiny_cluster():
+    for N in (1, 3):
+        sc, c = _ctx(10 + N, N, 2)
+        try:
+            info = B.celes_solve(c, 1e-12, mode=B.CELES_SOLVE_FP64, solver=B.CELES_SOLVER_BICGSTAB)
+            assert info["residual"] <= 1e-12
+            t = mie.t_diagonal(2, sc.k, sc.radii, sc.n_rel)
+            ain = incident.plane_wave_coeffs(2, sc.k, sc.positions, 0.0, 0.0, 2)
+            assert rel(B.celes_get_coefficients(c)[0], solve.solve_dense(sc.positions, sc.k, 2, t, ain)) <= 1e-10
+        finally:
+            B.celes_destroy(c)
+
+
+def test_empty_point_list_and_bad_indices():
+    sc, c = _ctx(20, 5, 2)
+    try:
+        B.celes_solve(c, 1e-10, mode=B.CELES_SOLVE_FP64)
+        assert B.celes_nearfield(c, np.zeros((0, 3))).shape == (0, 3)
+        with pytest.raises(B.CelesError):
+            B.celes_nearfield(c, np.ones((2, 3)), rhs=3)
+        with pytest.raises(B.CelesError):
+            B.celes_s11(c, [0.1, 0.2], rhs_a=0, rhs_b=5)
+        with pytest.raises(B.CelesError):
+            B.celes_power(c, n_beta=1)
+    finally:
+        B.celes_destroy(c)
