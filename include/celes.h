@@ -57,7 +57,7 @@ typedef enum {
 typedef enum { CELES_FP64 = 0, CELES_FP32 = 1 } celes_precision;
 
 typedef enum {
-  CELES_KERNEL_AUTO = 0,    /* rotation-translation-rotation for FP32, direct for FP64 */
+  CELES_KERNEL_AUTO = 0,    /* rotation-translation-rotation in both precisions */
   CELES_KERNEL_DIRECT = 1,  /* per-entry evaluation of W^{ij} (App. A.2 formula as printed) */
   CELES_KERNEL_RTR = 2      /* W = D^H W_z D (rotation, axial translation, rotation), both precisions */
 } celes_kernel;
@@ -163,8 +163,10 @@ int celes_master_matvec(celes_ctx* ctx, const void* x, void* y, int nrhs, int pr
 int celes_precond_build(celes_ctx* ctx, double cuboid_edge);
 
 /* y = P^{-1} x with P the block-diagonal part of M (Sec. 3.2.1, step 4):
- * per block, solve L_j U_j y = P_j x.  Layout as for the matvecs; FP32
- * vectors are solved with the FP64 factors.  x and y may be equal. */
+ * per block, solve L_j U_j y = P_j x.  Layout as for the matvecs.  FP64
+ * vectors use the FP64 factors; FP32 vectors an FP32 copy of them made at
+ * build time (the same operator wherever the FP32 solver applies it).  x and
+ * y may be equal. */
 int celes_precond_apply(celes_ctx* ctx, const void* x, void* y, int nrhs, int precision, void* stream);
 
 /* Provide an initial guess b0 ([nrhs][N][nmax] complex128, host) used by
@@ -319,6 +321,7 @@ int celes_coupling_matvec_noalloc(int64_t N, int lmax, double k, const double* p
 
 void celes_destroy(celes_ctx* ctx);
 const char* celes_last_error(const celes_ctx* ctx);
+
 /* ---- Batched solves over many ensembles (multi-RHS, uneven sizes) --------
  * A batch groups contexts (same device, any lmax and N, incident fields set)
  * and solves the master equation (I - T W) b = T a_in (Sec. 2.2) for every
@@ -341,8 +344,9 @@ const char* celes_last_error(const celes_ctx* ctx);
  *   ||T a - M b|| / ||T a|| <= tol per system; writes b into each context
  *   (read with celes_get_coefficients) and infos [count] (per context: max
  *   over its RHS; residual history not recorded).  opts may be NULL; its
- *   x0 must be CELES_X0_TA and its solver GMRES; use_precond is ignored.  Returns OK, ENOCONV
- *   (some system missed tol; b still written), ENUMERIC, ECUDA. */
+ *   x0 must be CELES_X0_TA and its solver GMRES; use_precond is ignored.
+ *   Returns OK, ENOCONV (some system missed tol; b still written), ENUMERIC,
+ *   ECUDA. */
 typedef struct celes_batch celes_batch;
 int celes_batch_create(celes_batch** out, celes_ctx* const* ctxs, int count, int restart);
 int celes_batch_num_systems(const celes_batch* b);

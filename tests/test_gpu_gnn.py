@@ -97,7 +97,7 @@ def _reference(sc, ctx, params, W, layers, L):
     loss = torch.mean((o - torch.tensor(tgt, dtype=torch.float32)) ** 2)
     loss.backward()
     grads = np.concatenate([np.concatenate([w.grad.numpy().ravel(), bb.grad.numpy()]) for (w, bb) in ts])
-    return float(loss), grads, shapes
+    return float(loss.detach()), grads, shapes
 
 
 def test_gnn_forward_and_backward_match_autograd():
