@@ -733,7 +733,7 @@ struct Gmres {
     std::vector<std::complex<double>> h;
     int s = dots(v, 1, v, h);
     if (s) return s;
-    out = std::sqrt(std::max(0.0, h[0].real()));
+    out = norm_from_dot(h[0].real());
     return CELES_OK;
   }
   // A v = M P^{-1} v
@@ -920,12 +920,12 @@ struct Bicgstab {
     std::complex<double> h[2];
     int s = dots(Wp(RH), 2, Wp(RR), h);  // [<r^, r>, <r, r>]
     if (s) return s;
-    const double r0 = std::sqrt(std::max(0.0, h[1].real()));
+    const double r0 = norm_from_dot(h[1].real());
+    if (!std::isfinite(r0)) return fail(c, CELES_ENUMERIC, "BiCGSTAB: non-finite residual");
     if (!(r0 > 0.0)) {
       rel_est = 0.0;
       return CELES_OK;
     }
-    if (!std::isfinite(r0)) return fail(c, CELES_ENUMERIC, "BiCGSTAB: non-finite residual");
     std::complex<double> rho = h[0], rho_prev = 1.0, alpha = 1.0, omega = 1.0;
     while (its < max_it) {
       if (std::abs(rho) == 0.0) break;  // breakdown: keep the current iterate
@@ -964,7 +964,7 @@ struct Bicgstab {
       s = dots(Wp(RH), 2, Wp(RR), h);
       if (s) return s;
       rho = h[0];
-      const double rn = std::sqrt(std::max(0.0, h[1].real()));
+      const double rn = norm_from_dot(h[1].real());
       if (!std::isfinite(rn)) return fail(c, CELES_ENUMERIC, "BiCGSTAB: non-finite residual");
       rel_est = rn / r0;
       if (hist) hist->push_back(rel_est * hist_scale);

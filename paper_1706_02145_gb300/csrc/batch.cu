@@ -164,19 +164,23 @@ __global__ void seg_scale_kernel(const VecSeg* __restrict__ seg, const double* _
   }
 }
 
-// y_s = sum_{j < nv} c[s][j] V_j,s     (c: [nsys][nv] complex128, zero-padded)
+// y_s = sum_{j < nv} c[s][j] V_j,s     (c: [nsys][m] complex128, zero-padded;
+// only the first nv <= m columns are read).  A zero coefficient skips its basis
+// vector: a system that stopped after k < nv steps never wrote V_k+1.. in its
+// segment, and 0 * (stale memory) may be NaN.
 template <typename R>
-__global__ void seg_combine_kernel(const VecSeg* __restrict__ seg, int nv, const Pair2<R>* __restrict__ V,
+__global__ void seg_combine_kernel(const VecSeg* __restrict__ seg, int m, int nv, const Pair2<R>* __restrict__ V,
                                    long long ldv, const double* __restrict__ c, Pair2<R>* __restrict__ y) {
   const int s = blockIdx.y;
   const VecSeg S = seg[s];
   if (!S.active) return;
-  const double* cs = c + (long long)s * nv * 2;
+  const double* cs = c + (long long)s * m * 2;
   for (int t = blockIdx.x * kSegThreads + threadIdx.x; t < S.n; t += kSegBlocks * kSegThreads) {
     R ar = 0, ai = 0;
     for (int j = 0; j < nv; ++j) {
-      const Pair2<R> v = V[j * ldv + S.off + t];
       const R cr = static_cast<R>(cs[2 * j]), ci = static_cast<R>(cs[2 * j + 1]);
+      if (cr == R(0) && ci == R(0)) continue;
+      const Pair2<R> v = V[j * ldv + S.off + t];
       ar = celes::fma_(cr, v.re, celes::fma_(-ci, v.im, ar));
       ai = celes::fma_(cr, v.im, celes::fma_(ci, v.re, ai));
     }
@@ -547,7 +551,7 @@ int lockstep_gmres(celes_batch* bt, const void* r, void* x, const std::vector<in
     const std::complex<double>* h = bt->hdots.as<std::complex<double>>();
     std::vector<double> sc(S, 0.0);
     for (int s = 0; s < S; ++s) {
-      rnorm[s] = std::sqrt(std::max(0.0, h[s].real()));
+      rnorm[s] = celes::norm_from_dot(h[s].real());
       if (!want[s]) continue;
       if (!std::isfinite(rnorm[s])) {
         bt->err = "batched GMRES: non-finite residual";
@@ -618,7 +622,7 @@ int lockstep_gmres(celes_batch* bt, const void* r, void* x, const std::vector<in
       std::vector<double> hn(S, 0.0), inv(S, 0.0);
       for (int s = 0; s < S; ++s) {
         if (!run[s]) continue;
-        hn[s] = std::sqrt(std::max(0.0, bt->hdots.as<std::complex<double>>()[s].real()));
+        hn[s] = celes::norm_from_dot(bt->hdots.as<std::complex<double>>()[s].real());
         if (!std::isfinite(hn[s])) {
           bt->err = "batched GMRES: non-finite Krylov vector";
           return CELES_ENUMERIC;
@@ -687,8 +691,11 @@ int lockstep_gmres(celes_batch* bt, const void* r, void* x, const std::vector<in
     if (st) return st;
     st = upload_coef(bt, coef);
     if (st) return st;
+    int kmax = 0;
+    for (int s = 0; s < S; ++s)
+      if (cycle[s]) kmax = std::max(kmax, kk_s[s]);
     BK(cudaMemsetAsync(bt->z.p, 0, vb, bt->stream), "zero");
-    seg_combine_kernel<R><<<sgrid, kSegThreads, 0, bt->stream>>>(bt->vseg.as<VecSeg>(), m,
+    seg_combine_kernel<R><<<sgrid, kSegThreads, 0, bt->stream>>>(bt->vseg.as<VecSeg>(), m, kmax,
                                                                   static_cast<const Pair2<R>*>(bt->V.p), n,
                                                                   bt->coef.as<double>(), static_cast<Pair2<R>*>(bt->z.p));
     flat_axpby_kernel<R, R><<<flat_blocks(n), 256, 0, bt->stream>>>(n, 1.0, static_cast<const Pair2<R>*>(bt->z.p), 1.0,
@@ -722,7 +729,11 @@ int lockstep_gmres(celes_batch* bt, const void* r, void* x, const std::vector<in
     any = false;
     for (int s = 0; s < S; ++s) {
       if (!again[s]) continue;
-      beta[s] = std::sqrt(std::max(0.0, bt->hdots.as<std::complex<double>>()[s].real()));
+      beta[s] = celes::norm_from_dot(bt->hdots.as<std::complex<double>>()[s].real());
+      if (!std::isfinite(beta[s])) {
+        bt->err = "batched GMRES: non-finite residual";
+        return CELES_ENUMERIC;
+      }
       rel_est[s] = beta[s] / rnorm[s];
       if (beta[s] <= tol[s] * rnorm[s] || !(beta[s] > 0.0)) continue;
       live[s] = 1;
@@ -940,7 +951,10 @@ extern "C" int celes_batch_solve(celes_batch* bt, double tol, const celes_solve_
   if (st) return st;
   st = seg_dots<double>(bt, bt->ta.p, 0, 1, bt->ta.p);
   if (st) return st;
-  for (int s = 0; s < S; ++s) tanorm[s] = std::sqrt(std::max(0.0, bt->hdots.as<std::complex<double>>()[s].real()));
+  for (int s = 0; s < S; ++s) {
+    tanorm[s] = celes::norm_from_dot(bt->hdots.as<std::complex<double>>()[s].real());
+    if (!std::isfinite(tanorm[s])) return batch_set_error(bt, CELES_ENUMERIC, "batch solve: non-finite T a");
+  }
   for (int it = 0; it <= o.max_outer; ++it) {
     // r = T a - (I - T W) b in FP64 for the systems not yet done
     std::vector<int> act(S, 0);
@@ -957,7 +971,7 @@ extern "C" int celes_batch_solve(celes_batch* bt, double tol, const celes_solve_
     bool all = true;
     for (int s = 0; s < S; ++s) {
       if (done[s]) continue;
-      const double rn = std::sqrt(std::max(0.0, bt->hdots.as<std::complex<double>>()[s].real()));
+      const double rn = celes::norm_from_dot(bt->hdots.as<std::complex<double>>()[s].real());
       rel[s] = tanorm[s] > 0.0 ? rn / tanorm[s] : 0.0;
       if (!std::isfinite(rel[s])) return batch_set_error(bt, CELES_ENUMERIC, "batch solve: non-finite residual");
       if (rel[s] <= tol || iters[s] >= o.max_iter) done[s] = 1;

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "../../include/celes.h"
@@ -10,6 +12,11 @@
 struct celes_ctx;
 
 namespace celes {
+
+// 2-norm from a reduced <v, v>: rounding may make a tiny value negative
+// (clamped to 0), but a NaN stays NaN so that the solvers' finiteness checks
+// see it (std::max(0.0, NaN) is 0.0)
+inline double norm_from_dot(double q) { return std::isnan(q) ? q : std::sqrt(std::max(0.0, q)); }
 
 // read-only view of a context's device data (for the learned-guess module)
 struct CtxView {

@@ -141,3 +141,37 @@ def test_batch_rejects_bad_use(batch_setup):
         assert B.load().celes_batch_solve(b, 1e-6, opts, info) == B.CELES_EINVAL
     finally:
         B.celes_batch_destroy(b)
+
+
+def test_batched_solve_ignores_stale_device_memory():
+    """Systems that stop their Krylov cycle at different steps leave the later
+    basis vectors of their segment unwritten; the update must not read them.
+    Device memory full of NaN is freed first, so that the batch's fresh buffers
+    are likely to reuse it (a plain first allocation would read as zeros)."""
+    junk = torch.full((48 * 1024 * 1024,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    del junk
+    torch.cuda.empty_cache()
+    ens = []
+    try:
+        for q, (N, L) in enumerate([(20, 2), (35, 3)]):
+            sc = synth.random_cluster(89, 10 + q, N, L, radius=100.0, fill=0.15, n=1.5 + 0.01j)
+            ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, L)
+            B.celes_set_incident(ctx, [B.make_incident("plane", beta=0.2, alpha=0.1, pol=2)])
+            ens.append((sc, ctx))
+        b = B.celes_batch_create([c for _, c in ens])
+        try:
+            code, infos = B.celes_batch_solve(b, len(ens), 1e-8, mode=B.CELES_SOLVE_MIXED)
+            assert code == B.CELES_OK
+        finally:
+            B.celes_batch_destroy(b)
+        for sc, ctx in ens:
+            L = sc.lmax
+            got = B.celes_get_coefficients(ctx)
+            assert np.all(np.isfinite(got))
+            t = mie.t_diagonal(L, sc.k, sc.radii, sc.n_rel)
+            a = incident.plane_wave_coeffs(L, sc.k, sc.positions, 0.2, 0.1, 2)
+            assert rel(got[0], solve.solve_dense(sc.positions, sc.k, L, t, a)) <= 1e-6
+    finally:
+        for _, ctx in ens:
+            B.celes_destroy(ctx)
