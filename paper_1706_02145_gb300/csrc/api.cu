@@ -758,11 +758,11 @@ struct Gmres {
     if (s) return s;
     its = 0;
     rel_est = 1.0;
+    if (!std::isfinite(rnorm)) return fail(c, CELES_ENUMERIC, "GMRES: non-finite residual");
     if (!(rnorm > 0.0)) {
       rel_est = 0.0;
       return CELES_OK;
     }
-    if (!std::isfinite(rnorm)) return fail(c, CELES_ENUMERIC, "GMRES: non-finite residual");
     // start: u = 0, residual r; restarts use the updated residual computed
     // from the Arnoldi relation (no extra matvec), tracked by beta
     CK(launch_axpby<R, R>(n, 1.0 / rnorm, r, 0.0, Vp(0), c->stream), "v0");
@@ -776,6 +776,7 @@ struct Gmres {
         double nb = 0.0;
         s = norm(w.p, nb);
         if (s) return s;
+        if (!std::isfinite(nb)) return fail(c, CELES_ENUMERIC, "GMRES: non-finite residual");
         beta = nb;
         if (beta <= tol * rnorm) break;
         CK(launch_axpby<R, R>(n, 1.0 / beta, w.p, 0.0, Vp(0), c->stream), "v0");
@@ -1194,6 +1195,7 @@ extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, 
         s = g32.norm(r32.p, rn);
         if (s) return s;
       }
+      if (!std::isfinite(rn)) return fail(c, CELES_ENUMERIC, "solve: non-finite residual");
       rel = rn / rhs_norm;
       hist.push_back(rel);
       while (true) {

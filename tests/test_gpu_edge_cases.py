@@ -88,3 +88,19 @@ def test_empty_point_list_and_bad_indices():
             B.celes_power(c, n_beta=1)
     finally:
         B.celes_destroy(c)
+
+
+@pytest.mark.parametrize("mode", [B.CELES_SOLVE_FP64, B.CELES_SOLVE_MIXED])
+@pytest.mark.parametrize("solver", [B.CELES_SOLVER_GMRES, B.CELES_SOLVER_BICGSTAB])
+def test_non_finite_first_iterate_is_a_numeric_error(mode, solver):
+    """A NaN user guess makes every residual NaN; the solve must report
+    CELES_ENUMERIC instead of reading NaN as converged (a clamp such as
+    max(0, NaN) returns 0)."""
+    sc, ctx = _ctx(11, 20, 2)
+    try:
+        B.celes_set_initial_guess(ctx, np.full((1, sc.N, sc.nmax), np.nan + 0j))
+        with pytest.raises(B.CelesError) as err:
+            B.celes_solve(ctx, 1e-8, mode=mode, x0=B.CELES_X0_USER, use_precond=False, solver=solver)
+        assert err.value.code == B.CELES_ENUMERIC
+    finally:
+        B.celes_destroy(ctx)
