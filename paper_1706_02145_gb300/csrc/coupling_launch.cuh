@@ -77,6 +77,12 @@ constexpr int kGenericRPB = 64;
 //   rotations (8 flops per R entry each), axial build (4 flops per term plus 4
 //   for the W+- combination per (mu >= 0, l, l') block), axial apply (2 complex
 //   MACs per (mu, l, l')), output phase (2 NH complex MACs), h_p recurrence.
+// f(integral_constant<l>) for l = 1 .. sizeof...(I)
+template <typename F, int... I>
+void for_each_degree(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I + 1>{}), ...);
+}
+
 template <int L>
 long long rtr_flops_per_pair_t() {
   long long f = 0;
@@ -89,8 +95,7 @@ long long rtr_flops_per_pair_t() {
     rot += 8LL * (2 * l + 1) * (2 * l + 1);
     dm += (2 * l + 1) + 2LL * rtr::DTab<l>::value.off[rtr::DTab<l>::value.ncanon];
   };
-  [&]<int... I>(std::integer_sequence<int, I...>) { (per_l(std::integral_constant<int, I + 1>{}), ...); }
-  (std::make_integer_sequence<int, L>{});
+  for_each_degree(per_l, std::make_integer_sequence<int, L>{});
   f += 2 * rot + 2 * dm;
   // axial entries: with the transpose symmetry only the entries lo <= li are
   // formed; every entry is applied to both rows
