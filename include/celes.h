@@ -175,7 +175,9 @@ int celes_set_initial_guess(celes_ctx* ctx, const double* b0_host);
 
 /* Solve M b = T a_in for every RHS to ||T a - M b|| / ||T a|| <= tol
  * (FP64 residual).  o and info may be NULL.  Returns CELES_ENOCONV if the
- * iteration budget ran out (the best b is still stored). */
+ * iteration budget ran out (the best b is still stored), CELES_ENUMERIC if a
+ * residual or Krylov vector norm is not finite (e.g. a NaN user guess) or
+ * GMRES meets a singular Hessenberg matrix; b is then not meaningful. */
 int celes_solve(celes_ctx* ctx, double tol, const celes_solve_opts* o, celes_solve_info* info);
 
 /* Copy results to the host ([nrhs][N][nmax] complex128). */
