@@ -270,6 +270,23 @@ def test_full_size_config2_sampled_rows():
         B.celes_destroy(ctx_d)
 
 
+def test_maximum_size_config5_sampled_rows():
+    """The largest workload (100 000 monodisperse spheres in a 4 um slab,
+    lmax 3, 1e10 ordered pairs) through the FP32 kernel in its default launch
+    shape: sampled receivers against the oracle's on-the-fly FP64 rows."""
+    sc = synth.config5(0)
+    ctx = make_ctx(sc)
+    try:
+        x = synth.random_vector(2, 78, (sc.N, sc.nmax))
+        y32 = gpu_matvec(ctx, x, B.CELES_FP32)
+        assert np.all(np.isfinite(y32))
+        rows = [0, sc.N - 1] + [int(r) for r in np.random.default_rng(6).choice(sc.N, 2, replace=False)]
+        ref = translation.coupling_matvec_rows(sc.positions, sc.k, sc.lmax, x, rows)
+        assert rel(y32[rows], ref) < 1e-5
+    finally:
+        B.celes_destroy(ctx)
+
+
 def test_overlap_and_argument_errors():
     pos = np.array([[0.0, 0.0, 0.0], [150.0, 0.0, 0.0]])
     with pytest.raises(B.CelesError) as e:
