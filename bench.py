@@ -191,6 +191,15 @@ def host_cores():
 # reference arm: the FP64 CPU oracle as it stands
 # ---------------------------------------------------------------------------
 
+def workload_config(N, L, world):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": f"Gaussian-beam slab: {N} polydisperse spheres (lognormal R, mean 150 nm), lmax {L}, "
+                        "n=1.5+0.001i, lambda 550 nm, cylinder slab fill 0.3, Gaussian beam w=2um; "
+                        "step = incident coefficients + FP32/FP64-refined GMRES to 1e-6 + far field",
+            "N": N, "lmax": L, "tol": TOL, "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "flushed between steps (256 MB write); inputs resident in HBM"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -215,8 +224,7 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"Gaussian-beam slab: {scene.N} polydisperse spheres, lmax {scene.lmax}, cylinder slab "
-                                   "fill 0.3, Gaussian beam w=2um", "N": scene.N, "lmax": scene.lmax},
+            "config": workload_config(scene.N, scene.lmax, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -540,11 +548,7 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": f"Gaussian-beam slab: {N} polydisperse spheres (lognormal R, mean 150 nm), lmax {L}, "
-                                       "n=1.5+0.001i, lambda 550 nm, cylinder slab fill 0.3, Gaussian beam w=2um; "
-                                       "step = incident coefficients + FP32/FP64-refined GMRES to 1e-6 + far field",
-                           "N": N, "lmax": L, "tol": TOL, "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "flushed between steps (256 MB write); inputs resident in HBM"},
+                "config": workload_config(N, L, world),
                 "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "batched": batched, "learned_guess": learned,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
