@@ -2,8 +2,29 @@
 
 The compute lives in ``_lib/libceles_gb300.so`` (CUDA, sm_103a) behind the C
 ABI of ``include/celes.h``; ``binding`` mirrors that ABI function by function
-(argument marshalling only) and ``Simulation`` is a small convenience wrapper
-that owns one context.
+(argument marshalling only).  The classes below own library handles:
+
+* ``Simulation``: one sphere cluster (positions and radii in nm, complex
+  refractive indices, vacuum wavelength, lmax) with its incident fields,
+  solve of (I - T W) b = T a_in, and the derived quantities.
+* ``BatchSolver``: every RHS of several Simulations (any lmax and size) in one
+  lockstep solve on the GPU.
+* ``LearnedGuess``: the graph network that predicts a first iterate.
+
+Typical use::
+
+    import paper_1706_02145_gb300 as celes
+    sim = celes.Simulation(positions, radii, n_sphere, 1.0, 550.0, lmax=4)
+    sim.set_incident([celes.make_incident("gaussian", waist=2000.0)])
+    sim.precond_build(900.0)                 # optional block preconditioner
+    info = sim.solve(1e-6)                   # FP32 GMRES, FP64 refinement
+    b = sim.coefficients()                   # [rhs][sphere][n] complex
+    g = sim.farfield(dirs)                   # (beta, alpha) directions
+    E = sim.nearfield(points)                # NaN inside spheres
+    sim.close()
+
+Every call runs on the GPU; there is no CPU fallback, and a missing or
+unloadable library raises.
 """
 
 from . import binding  # noqa: F401
