@@ -280,7 +280,8 @@ int celes_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, 
  *   celes_gnn_predict: computes the guess for every RHS of a context and
  *                      stores it for celes_solve with x0 = CELES_X0_LEARNED
  * The paper has no counterpart of the network itself; the final FP64 residual
- * of the solve judges it, and celes_solve falls back to T a_in per RHS. */
+ * of the solve decides whether it helped, and celes_solve falls back to
+ * T a_in per RHS when its residual is not smaller. */
 typedef struct celes_gnn celes_gnn;
 int celes_gnn_create(celes_gnn** out, int lmax, int width, int layers, int knn, uint64_t seed, int device);
 int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps, double lr, double* loss_out);

@@ -7,7 +7,7 @@
    backward GEMMs round their operands to BF16 as well).
 2. Training on solved ensembles lowers the loss; a solve started from the
    learned guess still reaches the FP64 residual tolerance and the oracle
-   solution (the residual is the judge; the solver falls back to T a).
+   solution (the residual decides; the solver falls back to T a).
 """
 
 import numpy as np
@@ -133,7 +133,7 @@ def test_gnn_training_and_learned_guess_solve():
                 B.celes_gnn_train(g, ctx, steps=1, lr=2e-3)
         last = [B.celes_gnn_train(g, ctx, steps=0) for _, ctx in train]
         assert np.mean(last) < 0.7 * np.mean(first)
-        # held-out ensemble: learned first iterate, FP64 residual as the judge
+        # held-out ensemble: learned first iterate, the FP64 residual decides
         sc = synth.random_cluster(41, 99, 160, L, radius=100.0, fill=0.25, n=1.55 + 0.01j)
         ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, L)
         try:
