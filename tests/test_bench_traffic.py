@@ -1,0 +1,40 @@
+"""bench.py reports a kernel's ncu DRAM traffic from profiles/ncu_traffic.json
+only while the coupling kernel sources hash to the value stored with it; a
+record taken on other source reads as null."""
+
+import importlib.util
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_traffic_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_committed_record_is_consistent():
+    b = _bench()
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+        rec = json.load(fh)["coupling_fp32_L4"]
+    assert rec["dram_bytes_per_launch"] == rec["dram_read"] + rec["dram_write"]
+    assert len(rec["source_hash"]) == 16 and "--clock-control none" in rec["command"]
+    expect = rec["dram_bytes_per_launch"] if rec["source_hash"] == b.kernel_source_hash() else None
+    assert b.ncu_traffic("coupling_fp32_L4") == expect
+
+
+def test_record_of_other_source_or_missing_key_reads_as_none(tmp_path, monkeypatch):
+    b = _bench()
+    (tmp_path / "profiles").mkdir()
+    rec = {"coupling_fp32_L4": {"dram_bytes_per_launch": 123, "dram_read": 100, "dram_write": 23,
+                                "source_hash": "0000000000000000"}}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    monkeypatch.setattr(b, "kernel_source_hash", lambda: "ffffffffffffffff")
+    assert b.ncu_traffic("coupling_fp32_L4") is None
+    assert b.ncu_traffic("no_such_kernel") is None
+    monkeypatch.setattr(b, "kernel_source_hash", lambda: "0000000000000000")
+    assert b.ncu_traffic("coupling_fp32_L4") == 123
