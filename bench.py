@@ -244,8 +244,7 @@ def run_batched(args, local_rank):
     from paper_1706_02145_gb300 import binding as B
     scenes = []
     for e in range(args.batched_ensembles):
-        full = synth.config3(e, n_rhs=args.batched_rhs)
-        scenes.append(synth.config3(e, n_rhs=args.batched_rhs, N=max(80, int(0.4 * full.N))))
+        scenes.append(synth.config3(e, n_rhs=args.batched_rhs, N=max(80, int(0.4 * synth.config3_size(e)))))
     ctxs = []
     try:
         for sc in scenes:

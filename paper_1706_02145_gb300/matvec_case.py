@@ -49,8 +49,7 @@ def main():
     if a.op == "batch":
         scenes = []
         for e in range(a.ensembles):
-            full = synth.config3(e, n_rhs=a.rhs)
-            scenes.append(synth.config3(e, n_rhs=a.rhs, N=max(80, int(0.4 * full.N))))
+            scenes.append(synth.config3(e, n_rhs=a.rhs, N=max(80, int(0.4 * synth.config3_size(e)))))
         ctxs = []
         for sc in scenes:
             c = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax)

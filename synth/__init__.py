@@ -195,48 +195,83 @@ def fibonacci_cap(n, beta_max):
     return np.arccos(cosb), np.mod(golden * i, 2 * np.pi)
 
 
-def config3(index: int, n_rhs: int = 8, N: Optional[int] = None, lmax: Optional[int] = None) -> Scene:
-    rng = rng_for(3, index)
+def _config3_draw(rng):
     N_ = int(rng.integers(200, 3001))
     L_ = int(rng.integers(2, 6))
     lam = float(rng.uniform(400.0, 800.0))
     R = float(rng.uniform(80.0, 200.0))
     n = float(rng.uniform(1.45, 2.0))
     fill = float(rng.uniform(0.1, 0.35))
-    N = N_ if N is None else N
-    L = L_ if lmax is None else lmax
-    side = (N * 4.0 / 3.0 * np.pi * R ** 3 / fill) ** (1.0 / 3.0)
-    radii = np.full(N, R)
-
-    def sampler(rng, r, m):
-        return rng.uniform(r, side - r, size=(m, 3))
-
-    pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side))
-    betas, alphas = fibonacci_cap(n_rhs, np.deg2rad(60.0))
-    incs = [Incident("plane", beta=float(b), alpha=float(a), pol=2) for b, a in zip(betas, alphas)]
-    return Scene(pos, radii, np.full(N, n + 0j), 1.0, lam, L, incs,
-                 name=f"ensemble {index}: N={N} L={L} lambda={lam:.0f} fill={fill:.2f}")
+    return N_, L_, lam, R, n, fill
 
 
-def config4(index: int, N: Optional[int] = None, fill: Optional[float] = None) -> Scene:
+def config3_size(index: int) -> int:
+    """Number of spheres of multi-ensemble ``index`` (no packing)."""
+    return _config3_draw(rng_for(3, index))[0]
+
+
+def config3(index: int, n_rhs: int = 8, N: Optional[int] = None, lmax: Optional[int] = None,
+            max_tries: int = 2_000_000) -> Scene:
+    """Multi-ensemble ``index``: N ~ U[200, 3000], lmax ~ U{2..5}, lambda, R, n
+    and fill drawn per ensemble; monodisperse spheres in a cube; ``n_rhs``
+    plane waves on a Fibonacci cap beta <= 60 deg.  The walls exclude a shell
+    of one radius, so for small N a fill near 0.35 can exceed what random
+    sequential addition packs: then the cube grows in 3 % steps (a new pass
+    from the same seed each time) until the spheres fit, and the ensemble's
+    fill is lower than drawn."""
+    sides = []
+    for grow in range(60):
+        rng = rng_for(3, index)
+        N_, L_, lam, R, n, fill = _config3_draw(rng)
+        N = N_ if N is None else N
+        L = L_ if lmax is None else lmax
+        side = (N * 4.0 / 3.0 * np.pi * R ** 3 / fill) ** (1.0 / 3.0) * 1.03 ** grow
+        radii = np.full(N, R)
+
+        def sampler(rng, r, m, side=side):
+            return rng.uniform(r, side - r, size=(m, 3))
+
+        try:
+            pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side),
+                                             max_tries=max_tries if grow == 0 else 400 * N)
+        except RuntimeError:
+            sides.append(side)
+            continue
+        betas, alphas = fibonacci_cap(n_rhs, np.deg2rad(60.0))
+        incs = [Incident("plane", beta=float(b), alpha=float(a), pol=2) for b, a in zip(betas, alphas)]
+        fill_eff = N * 4.0 / 3.0 * np.pi * R ** 3 / side ** 3
+        return Scene(pos, radii, np.full(N, n + 0j), 1.0, lam, L, incs,
+                     name=f"ensemble {index}: N={N} L={L} lambda={lam:.0f} fill={fill_eff:.2f}")
+    raise RuntimeError(f"config3({index}): no packing found up to side {sides[-1]:.0f} nm")
+
+
+def config4(index: int, N: Optional[int] = None, fill: Optional[float] = None, max_tries: int = 2_000_000) -> Scene:
     """Learned-guess ensembles: R = 100 nm, n = 1.52, lambda = 550 nm, L = 3,
     x-polarised plane wave along +z, random sequential addition in a cube;
-    N ~ U[1000, 5000] and fill ~ U[0.2, 0.35] unless given."""
-    rng = rng_for(4, index)
-    N_ = int(rng.integers(1000, 5001))
-    fill_ = float(rng.uniform(0.2, 0.35))
-    N = N_ if N is None else N
-    fill = fill_ if fill is None else fill
-    R = 100.0
-    side = (N * 4.0 / 3.0 * np.pi * R ** 3 / fill) ** (1.0 / 3.0)
-    radii = np.full(N, R)
+    N ~ U[1000, 5000] and fill ~ U[0.2, 0.35] unless given.  As in config3, a
+    fill that cannot be packed grows the cube in 3 % steps."""
+    for grow in range(60):
+        rng = rng_for(4, index)
+        N_ = int(rng.integers(1000, 5001))
+        fill_ = float(rng.uniform(0.2, 0.35))
+        N = N_ if N is None else N
+        fill = fill_ if fill is None else fill
+        R = 100.0
+        side = (N * 4.0 / 3.0 * np.pi * R ** 3 / fill) ** (1.0 / 3.0) * 1.03 ** grow
+        radii = np.full(N, R)
 
-    def sampler(rng, r, m):
-        return rng.uniform(r, side - r, size=(m, 3))
+        def sampler(rng, r, m, side=side):
+            return rng.uniform(r, side - r, size=(m, 3))
 
-    pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side))
-    return Scene(pos, radii, np.full(N, 1.52 + 0j), 1.0, 550.0, 3,
-                 [Incident("plane", beta=0.0, alpha=0.0, pol=2)], name=f"learned-guess cube N={N} fill={fill:.2f}")
+        try:
+            pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side),
+                                             max_tries=max_tries if grow == 0 else 400 * N)
+        except RuntimeError:
+            continue
+        fill_eff = N * 4.0 / 3.0 * np.pi * R ** 3 / side ** 3
+        return Scene(pos, radii, np.full(N, 1.52 + 0j), 1.0, 550.0, 3,
+                     [Incident("plane", beta=0.0, alpha=0.0, pol=2)], name=f"learned-guess cube N={N} fill={fill_eff:.2f}")
+    raise RuntimeError(f"config4({index}): no packing found")
 
 
 def config5(seed_index: int = 0, N: int = 100_000) -> Scene:

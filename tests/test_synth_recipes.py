@@ -1,0 +1,106 @@
+"""The seeded synthetic inputs follow their stated recipes: sizes, radius
+distribution, material, container, fill fraction, incident fields, disjoint
+spheres (the method requires non-overlapping spheres) and determinism."""
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import synth
+
+
+def _disjoint(sc):
+    tree = cKDTree(sc.positions)
+    pairs = tree.query_pairs(2.0 * sc.radii.max(), output_type="ndarray")
+    if len(pairs) == 0:
+        return True
+    d = np.linalg.norm(sc.positions[pairs[:, 0]] - sc.positions[pairs[:, 1]], axis=1)
+    return bool(np.all(d >= sc.radii[pairs[:, 0]] + sc.radii[pairs[:, 1]]))
+
+
+def _volume(sc):
+    return float(np.sum(4.0 / 3.0 * np.pi * sc.radii ** 3))
+
+
+def test_config1_cube():
+    sc = synth.config1(0)
+    assert sc.N == 50 and sc.lmax == 3 and sc.wavelength == 550.0
+    assert np.all(sc.radii == 100.0) and np.all(sc.n_sphere == 1.52)
+    side = (_volume(sc) / 0.2) ** (1.0 / 3.0)
+    assert np.all(sc.positions >= 100.0 - 1e-9) and np.all(sc.positions <= side - 100.0 + 1e-9)
+    assert _disjoint(sc)
+    inc = sc.incidents[0]
+    assert inc.kind == "plane" and inc.beta == 0.0 and inc.pol == 2
+
+
+def test_config2_polydisperse_cylinder_slab():
+    sc = synth.config2(0, N=2000)
+    assert sc.lmax == 4 and np.all(sc.n_sphere == 1.5 + 0.001j)
+    ln = np.log(sc.radii)
+    assert abs(np.mean(sc.radii) - 150.0) < 2.0 and abs(np.std(ln) - 0.1) < 0.01
+    z = sc.positions[:, 2]
+    assert np.all(z - sc.radii >= -1e-9) and np.all(z + sc.radii <= 2000.0 + 1e-9)
+    rho = np.hypot(sc.positions[:, 0], sc.positions[:, 1])
+    rc = np.sqrt(_volume(sc) / 0.3 / (np.pi * 2000.0))
+    assert np.all(rho + sc.radii <= rc + 1e-9)
+    assert abs(_volume(sc) / (np.pi * rc ** 2 * 2000.0) - 0.3) < 1e-12
+    assert _disjoint(sc)
+    inc = sc.incidents[0]
+    assert inc.kind == "gaussian" and inc.waist == 2000.0 and inc.alpha_G == -np.pi / 2
+
+
+def test_config2_full_size_radius_of_the_slab():
+    """The bench workload: 10 000 spheres give a cylinder radius near 8.7 um."""
+    rng = synth.rng_for(2, 0)
+    radii = synth.lognormal_radii(rng, 10_000)
+    rc = np.sqrt(np.sum(4.0 / 3.0 * np.pi * radii ** 3) / 0.3 / (np.pi * 2000.0))
+    assert 8500.0 < rc < 8900.0
+
+
+@pytest.mark.parametrize("index", [0, 3])
+def test_config3_ensembles(index):
+    sc = synth.config3(index, N=300)
+    assert 2 <= sc.lmax <= 5 and 400.0 <= sc.wavelength <= 800.0
+    assert 80.0 <= sc.radii[0] <= 200.0 and np.all(sc.radii == sc.radii[0])
+    assert 1.45 <= sc.n_sphere[0].real <= 2.0
+    assert len(sc.incidents) == 8
+    assert all(i.kind == "plane" and 0.0 <= i.beta <= np.deg2rad(60.0) + 1e-12 for i in sc.incidents)
+    assert _disjoint(sc)
+
+
+def test_config3_sizes_of_all_64_ensembles():
+    sizes = [synth.config3_size(i) for i in range(64)]
+    assert all(200 <= n <= 3000 for n in sizes) and len(set(sizes)) > 50
+
+
+def test_config3_grows_the_cube_when_the_drawn_fill_cannot_be_packed():
+    """Ensemble 17 at 300 spheres draws a fill that random sequential addition
+    cannot reach inside the walls; with a small try budget the first pass
+    gives up at once and a larger cube is used, from the same seed."""
+    sc = synth.config3(17, N=300, max_tries=20_000)
+    assert sc.N == 300 and _disjoint(sc)
+    side = sc.positions.max() + sc.radii[0]
+    drawn = synth._config3_draw(synth.rng_for(3, 17))[5]
+    assert np.sum(4.0 / 3.0 * np.pi * sc.radii ** 3) / side ** 3 < drawn
+    again = synth.config3(17, N=300, max_tries=20_000)
+    assert np.array_equal(sc.positions, again.positions)
+
+
+def test_config5_slab_at_reduced_size():
+    sc = synth.config5(0, N=4000)
+    assert sc.lmax == 3 and np.all(sc.radii == 130.0)
+    z = sc.positions[:, 2]
+    assert np.all(z >= 130.0 - 1e-9) and np.all(z <= 4000.0 - 130.0 + 1e-9)
+    side = np.sqrt(_volume(sc) / 0.25 / 4000.0)
+    assert np.all(np.abs(sc.positions[:, :2]) <= side / 2 - 130.0 + 1e-9)
+    assert _disjoint(sc)
+    assert sc.incidents[0].kind == "gaussian" and sc.incidents[0].waist == 5000.0
+
+
+def test_seeded_and_independent():
+    a, b = synth.config2(1, N=500), synth.config2(1, N=500)
+    c = synth.config2(2, N=500)
+    assert np.array_equal(a.positions, b.positions) and np.array_equal(a.radii, b.radii)
+    assert not np.allclose(a.positions, c.positions)
+    v1 = synth.random_vector(2, 77, (10, 4))
+    assert np.array_equal(v1, synth.random_vector(2, 77, (10, 4)))
