@@ -332,6 +332,7 @@ void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vect
 // ---------------------------------------------------------------------------
 extern "C" int celes_create(celes_ctx** out, int64_t N, const double* positions, const double* radii,
                             const double* n_i, double n0, double k0, int lmax, const celes_options* opt) {
+  celes::NvtxRange nvtx_range_("celes_create");
   if (!out) return CELES_EINVAL;
   *out = nullptr;
   if (N < 1 || !positions || !radii || !n_i || lmax < 1 || lmax > 5 || !(n0 > 0.0) || !(k0 > 0.0) ||
@@ -521,6 +522,7 @@ extern "C" int celes_coupling_terms(int lmax, int* idx, double* val, int cap) {
 // incident field
 // ---------------------------------------------------------------------------
 extern "C" int celes_set_incident(celes_ctx* c, const celes_incident* inc, int nrhs) {
+  celes::NvtxRange nvtx_range_("celes_set_incident");
   if (!c) return CELES_EINVAL;
   if (!inc || nrhs < 1) return fail(c, CELES_EINVAL, "set_incident: need nrhs >= 1 descriptors");
   for (int r = 0; r < nrhs; ++r) {
@@ -598,6 +600,7 @@ extern "C" int celes_master_matvec(celes_ctx* c, const void* x, void* y, int nrh
 }
 
 extern "C" int celes_precond_build(celes_ctx* c, double edge) {
+  celes::NvtxRange nvtx_range_("celes_precond_build");
   if (!c) return CELES_EINVAL;
   if (!(edge > 0.0)) return fail(c, CELES_EINVAL, "precond_build: edge must be > 0");
   DeviceGuard dg(c->device);
@@ -1063,6 +1066,7 @@ extern "C" int celes_set_initial_guess(celes_ctx* c, const double* b0) {
 }
 
 extern "C" int celes_solve(celes_ctx* c, double tol, const celes_solve_opts* o, celes_solve_info* info) {
+  celes::NvtxRange nvtx_range_("celes_solve");
   if (!c) return CELES_EINVAL;
   if (c->nrhs < 1) return fail(c, CELES_ESTATE, "solve: call set_incident first");
   if (!(tol > 0.0)) return fail(c, CELES_EINVAL, "solve: tol must be > 0");
@@ -1285,6 +1289,7 @@ extern "C" int celes_get_tmatrix(celes_ctx* c, double* out) {
 }
 
 extern "C" int celes_farfield(celes_ctx* c, const double* dirs, int64_t Nd, double* g, int rhs) {
+  celes::NvtxRange nvtx_range_("celes_farfield");
   if (!c) return CELES_EINVAL;
   if (!dirs || !g || Nd < 1) return fail(c, CELES_EINVAL, "farfield: bad arguments");
   if (!c->has_b) return fail(c, CELES_ESTATE, "farfield: no solution yet");

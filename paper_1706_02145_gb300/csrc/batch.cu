@@ -763,6 +763,7 @@ int batch_set_error(celes_batch* bt, int code, const char* msg) {
 }  // namespace
 
 extern "C" int celes_batch_create(celes_batch** out, celes_ctx* const* ctxs, int count, int restart) {
+  celes::NvtxRange nvtx_range_("celes_batch_create");
   if (!out) return CELES_EINVAL;
   *out = nullptr;
   if (!ctxs || count < 1) return CELES_EINVAL;
@@ -903,6 +904,7 @@ extern "C" int celes_batch_master_matvec(celes_batch* bt, const void* x, void* y
 }
 
 extern "C" int celes_batch_solve(celes_batch* bt, double tol, const celes_solve_opts* opts, celes_solve_info* infos) {
+  celes::NvtxRange nvtx_range_("celes_batch_solve");
   if (!bt || !(tol > 0.0)) return CELES_EINVAL;
   celes_solve_opts o{};
   o.mode = CELES_SOLVE_MIXED;

@@ -731,6 +731,7 @@ extern "C" void celes_gnn_destroy(celes_gnn* g) {
 }
 
 extern "C" int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps, double lr, double* loss_out) {
+  celes::NvtxRange nvtx_range_("celes_gnn_train");
   if (!g || !ctx || steps < 0 || !(lr > 0.0)) return CELES_EINVAL;
   CtxView v{};
   int s = ctx_view(ctx, &v);
@@ -780,6 +781,7 @@ extern "C" int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps,
 }
 
 extern "C" int celes_gnn_predict(celes_gnn* g, celes_ctx* ctx) {
+  celes::NvtxRange nvtx_range_("celes_gnn_predict");
   if (!g || !ctx) return CELES_EINVAL;
   CtxView v{};
   int s = ctx_view(ctx, &v);

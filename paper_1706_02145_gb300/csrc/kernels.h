@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -17,6 +18,15 @@ namespace celes {
 // (clamped to 0), but a NaN stays NaN so that the solvers' finiteness checks
 // see it (std::max(0.0, NaN) is 0.0)
 inline double norm_from_dot(double q) { return std::isnan(q) ? q : std::sqrt(std::max(0.0, q)); }
+
+// named NVTX range over one API call (shows the phases in a profiler's
+// timeline; a no-op when no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // read-only view of a context's device data (for the learned-guess module)
 struct CtxView {

@@ -195,6 +195,7 @@ void gauss_legendre_nodes(int n, double a, double b, std::vector<double>& x, std
 }  // namespace celes
 
 extern "C" int celes_nearfield(celes_ctx* ctx, const double* points, int64_t Np, int rhs, int what, double* E) {
+  celes::NvtxRange nvtx_range_("celes_nearfield");
   using namespace celes;
   if (!ctx || Np < 0 || (Np > 0 && (!points || !E)) || what < 0 || what > 2) return CELES_EINVAL;
   CtxView v{};

@@ -65,6 +65,7 @@ __global__ void power_sum_kernel(int64_t Nd, int64_t nfwd, const double* __restr
 }  // namespace celes
 
 extern "C" int celes_power(celes_ctx* ctx, int rhs, int n_beta, int n_alpha, double* R, double* T) {
+  celes::NvtxRange nvtx_range_("celes_power");
   using namespace celes;
   if (!ctx || !R || !T || n_beta < 2 || n_beta > 8192 || n_alpha < 4 || n_alpha > 65536) return CELES_EINVAL;
   CtxView v{};
@@ -179,6 +180,7 @@ __global__ void s11_kernel(int n_alpha, const double* __restrict__ ga, const dou
 
 extern "C" int celes_s11(celes_ctx* ctx, int rhs_a, int rhs_b, const double* betas, int n_beta, int n_alpha,
                          double* s11) {
+  celes::NvtxRange nvtx_range_("celes_s11");
   using namespace celes;
   if (!ctx || !betas || !s11 || n_beta < 1 || n_alpha < 1 || n_alpha > 1 << 20) return CELES_EINVAL;
   CtxView v{};

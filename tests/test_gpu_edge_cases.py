@@ -104,3 +104,41 @@ def test_non_finite_first_iterate_is_a_numeric_error(mode, solver):
         assert err.value.code == B.CELES_ENUMERIC
     finally:
         B.celes_destroy(ctx)
+
+
+def test_resume_from_a_saved_solution():
+    """Checkpoint and resume through the custom initial condition: a solve
+    stopped at 1e-4 and restarted in a new context from its saved b reaches
+    the same answer as a solve from T a, in fewer iterations."""
+    sc, ctx = _ctx(12, 40, 3)
+    sc2, ctx2 = _ctx(12, 40, 3)
+    try:
+        B.celes_solve(ctx, 1e-4, mode=B.CELES_SOLVE_FP64, use_precond=False)
+        saved = B.celes_get_coefficients(ctx)
+        scratch = B.celes_solve(ctx, 1e-10, mode=B.CELES_SOLVE_FP64, use_precond=False, x0=B.CELES_X0_TA)
+        b_ref = B.celes_get_coefficients(ctx)
+        B.celes_set_initial_guess(ctx2, saved)
+        resumed = B.celes_solve(ctx2, 1e-10, mode=B.CELES_SOLVE_FP64, use_precond=False, x0=B.CELES_X0_USER)
+        assert resumed["residual"] <= 1e-10 and resumed["guess_used"] >= 1
+        assert resumed["iterations"] < scratch["iterations"]
+        assert rel(B.celes_get_coefficients(ctx2), b_ref) < 1e-8
+    finally:
+        B.celes_destroy(ctx)
+        B.celes_destroy(ctx2)
+
+
+def test_preconditioner_too_large_for_the_device_is_enomem():
+    """One cuboid holding 3000 spheres at lmax 4 needs 332 GB of FP64 LU
+    factors, more than the GPU has: the build fails with CELES_ENOMEM before
+    any kernel runs, and the context still solves without it."""
+    sc = synth.config2(0, N=3000)
+    ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax)
+    try:
+        B.celes_set_incident(ctx, [B.make_incident("plane", beta=0.0, alpha=0.0, pol=2)])
+        with pytest.raises(B.CelesError) as err:
+            B.celes_precond_build(ctx, 1.0e7)
+        assert err.value.code == B.CELES_ENOMEM
+        info = B.celes_solve(ctx, 1e-6, mode=B.CELES_SOLVE_MIXED)
+        assert info["residual"] <= 1e-6
+    finally:
+        B.celes_destroy(ctx)
