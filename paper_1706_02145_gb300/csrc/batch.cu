@@ -755,6 +755,20 @@ int lockstep_gmres(celes_batch* bt, const void* r, void* x, const std::vector<in
   return CELES_OK;
 }
 
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+};
+
 int batch_set_error(celes_batch* bt, int code, const char* msg) {
   if (bt) bt->err = msg;
   return code;
@@ -937,9 +951,8 @@ extern "C" int celes_batch_solve(celes_batch* bt, double tol, const celes_solve_
       bt->dots.ensure((size_t)S * (m + 2) * 16) != cudaSuccess || bt->coef.ensure((size_t)S * (m + 2) * 16) != cudaSuccess ||
       bt->hdots.ensure((size_t)S * (m + 2) * 16) != cudaSuccess)
     return batch_set_error(bt, CELES_ENOMEM, "batch solve: device memory");
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
+  EventPair ev;  // solve time; released on every return path
+  const cudaEvent_t t0 = ev.a, t1 = ev.b;
   cudaEventRecord(t0, bt->stream);
   // b = T a
   if (cudaMemcpyAsync(bt->b.p, bt->ta.p, n * 16, cudaMemcpyDeviceToDevice, bt->stream) != cudaSuccess)
@@ -1030,8 +1043,6 @@ extern "C" int celes_batch_solve(celes_batch* bt, double tol, const celes_solve_
   if (cudaStreamSynchronize(bt->stream) != cudaSuccess) return CELES_ECUDA;
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, t0, t1);
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
   for (celes_ctx* c : bt->ctx) celes::ctx_mark_solved(c);
   bool all_ok = true;
   for (int s = 0; s < S; ++s) all_ok = all_ok && rel[s] <= tol;
