@@ -752,25 +752,29 @@ extern "C" int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps,
     if (!s) {
       target_kernel<<<blocks(n), 256, 0, g->stream>>>(n, v.b + (size_t)rhs * n, v.rhs + (size_t)rhs * n, scale,
                                                        tmp.as<float>());
-      cudaMemsetAsync(g->tgt.p, 0, N * g->OUTP * 4, g->stream);
-      cudaMemcpy2DAsync(g->tgt.p, g->OUTP * 4, tmp.p, v.nmax * 2 * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
-                        g->stream);
       note_launch();
+      if (cudaMemsetAsync(g->tgt.p, 0, N * g->OUTP * 4, g->stream) != cudaSuccess ||
+          cudaMemcpy2DAsync(g->tgt.p, g->OUTP * 4, tmp.p, v.nmax * 2 * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
+                            g->stream) != cudaSuccess)
+        s = CELES_ECUDA;
       double loss = 0.0;
       // steps = 0: loss and gradients only (no update)
       const int passes = steps > 0 ? steps : 1;
       for (int it = 0; it < passes && !s; ++it) {
         s = forward(g, N);
         if (s) break;
-        cudaMemsetAsync(g->lossd.p, 0, 8, g->stream);
+        if (cudaMemsetAsync(g->lossd.p, 0, 8, g->stream) != cudaSuccess) {
+          s = CELES_ECUDA;
+          break;
+        }
         mse_kernel<<<256, 256, 0, g->stream>>>(N * g->OUTP, g->o.as<float>(), g->tgt.as<float>(),
                                                g->dout.as<float>(), g->lossd.as<double>());
         note_launch();
         s = backward(g, N);
         if (!s && steps > 0) s = adam(g, static_cast<float>(lr));
-        if (!s && it == passes - 1) {
-          cudaMemcpyAsync(&loss, g->lossd.p, 8, cudaMemcpyDeviceToHost, g->stream);
-        }
+        if (!s && it == passes - 1 &&
+            cudaMemcpyAsync(&loss, g->lossd.p, 8, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+          s = CELES_ECUDA;
       }
       if (!s) s = check_err(g);
       if (!s && loss_out) *loss_out = loss;
@@ -799,8 +803,11 @@ extern "C" int celes_gnn_predict(celes_gnn* g, celes_ctx* ctx) {
     s = prepare(g, v, r, scale);
     if (!s) s = forward(g, N);
     if (!s) {
-      cudaMemcpy2DAsync(o2.p, v.nmax * 2 * 4, g->o.p, g->OUTP * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
-                        g->stream);
+      if (cudaMemcpy2DAsync(o2.p, v.nmax * 2 * 4, g->o.p, g->OUTP * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
+                            g->stream) != cudaSuccess) {
+        s = CELES_ECUDA;
+        break;
+      }
       guess_kernel<<<blocks(n), 256, 0, g->stream>>>(n, v.rhs + (size_t)r * n, o2.as<float>(), 1.0 / scale,
                                                      b0.as<double>());
       note_launch();
