@@ -224,8 +224,12 @@ extern "C" int celes_nearfield(celes_ctx* ctx, const double* points, int64_t Np,
     cleanup();
     return CELES_ENOMEM;
   }
-  cudaMemcpyAsync(dp, points, sizeof(double) * 3 * Np, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(dE, 0, sizeof(double) * 6 * Np, st);
+  cudaError_t e = cudaMemcpyAsync(dp, points, sizeof(double) * 3 * Np, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dE, 0, sizeof(double) * 6 * Np, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return CELES_ECUDA;
+  }
   if (what != 1) {
     const double* b = v.b + (size_t)rhs * v.N * v.nmax * 2;
     nearfield_scattered_kernel<<<nblocks(Np), kNfThreads, 0, st>>>(Np, dp, v.N, v.L, v.k,
@@ -248,15 +252,18 @@ extern "C" int celes_nearfield(celes_ctx* ctx, const double* points, int64_t Np,
         cleanup();
         return CELES_ENOMEM;
       }
-      cudaMemcpyAsync(dn, hx.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
-      cudaMemcpyAsync(dw, hw.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st);
+      if (cudaMemcpyAsync(dn, hx.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(dw, hw.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cleanup();
+        return CELES_ECUDA;
+      }
       nearfield_gauss_kernel<<<nblocks(Np), kNfThreads, 0, st>>>(Np, dp, v.k, d.waist, d.focus[0], d.focus[1],
                                                                  d.focus[2], d.alpha_G, d.E0_re, d.E0_im, nb, dn, dw,
                                                                  dE);
     }
     note_launch();
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(E, dE, sizeof(double) * 6 * Np, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cleanup();
