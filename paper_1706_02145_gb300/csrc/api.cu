@@ -256,9 +256,16 @@ int auto_chunks(const celes_ctx* c, int precision) {
 // coupling (mode 0: y = W x) or master (mode 1: y = x - T W x) products
 int prof_begin(celes_ctx* c, cudaStream_t st, celes_ctx::Rec& r, int which) {
   r.which = which;
-  CK(cudaEventCreate(&r.a), "event");
-  CK(cudaEventCreate(&r.b), "event");
-  CK(cudaEventRecord(r.a, st), "event");
+  r.a = r.b = nullptr;
+  cudaError_t e = cudaEventCreate(&r.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&r.b);
+  if (e == cudaSuccess) e = cudaEventRecord(r.a, st);
+  if (e != cudaSuccess) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+    r.a = r.b = nullptr;
+    return cuda_fail(c, e, "event");
+  }
   return CELES_OK;
 }
 
