@@ -91,3 +91,18 @@ def test_create_rejects_bad_arguments_before_touching_a_gpu(lib):
     code = lib.celes_create(ctypes.byref(ctx), 2, pos.ctypes.data_as(dp), rad.ctypes.data_as(dp),
                             ni.ctypes.data_as(dp), 1.0, 0.01, 9, None)
     assert code == binding.CELES_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every call raises."""
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libceles_gb300.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.celes_create(np.zeros((1, 3)), np.ones(1), np.full(1, 1.5 + 0j), 1.0, 0.01, 2)
+
+
+def test_every_binding_signature_names_an_exported_symbol(lib):
+    for name, _, _ in binding.SIGNATURES:
+        assert hasattr(lib, name), name
