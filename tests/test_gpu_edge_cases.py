@@ -142,3 +142,33 @@ def test_preconditioner_too_large_for_the_device_is_enomem():
         assert info["residual"] <= 1e-6
     finally:
         B.celes_destroy(ctx)
+
+
+@pytest.mark.parametrize("kernel", [B.CELES_KERNEL_RTR, B.CELES_KERNEL_DIRECT])
+def test_aligned_and_nearly_aligned_pairs(kernel):
+    """A cubic lattice (pairs exactly along the axes and diagonals: theta = 0
+    or pi, where phi is undefined) and a column of spheres 0, 1e-3 and 1e-6 nm
+    off the z axis: both precisions against the oracle's dense W."""
+    from oracle import translation
+    g = np.arange(3) * 250.0
+    lattice = np.array([[x, y, z] for x in g for y in g for z in g])
+    column = np.array([[800.0 + dx, 0.0, 260.0 * q] for q, dx in enumerate([0.0, 1e-3, 1e-6, 0.0, 2e-3])])
+    pos = np.concatenate([lattice, column])
+    N, L = len(pos), 4
+    radii = np.full(N, 100.0)
+    k0 = 2.0 * np.pi / 550.0
+    ctx = B.celes_create(pos, radii, np.full(N, 1.5 + 0.01j), 1.0, k0, L, kernel=kernel)
+    try:
+        nmax = 2 * L * (L + 2)
+        x = synth.random_vector(2, 91, (N, nmax))
+        ref = (translation.coupling_matrix(pos, k0, L) @ x.reshape(-1)).reshape(N, nmax)
+        for precision, dt, tol in [(B.CELES_FP64, torch.complex128, 1e-10), (B.CELES_FP32, torch.complex64, 1e-5)]:
+            xd = torch.from_numpy(x).to(dt).cuda()
+            yd = torch.zeros_like(xd)
+            B.celes_coupling_matvec(ctx, xd, yd, precision=precision)
+            torch.cuda.synchronize()
+            y = yd.cpu().numpy().astype(np.complex128)
+            assert np.all(np.isfinite(y))
+            assert rel(y, ref) < tol, (precision, rel(y, ref))
+    finally:
+        B.celes_destroy(ctx)
