@@ -110,3 +110,24 @@ def test_coupling_matrix_blocks_and_on_the_fly_rows():
     rows = [0, 3, 4]
     yr = translation.coupling_matvec_rows(pos, K, L, x, rows)
     assert np.allclose(yr, y[rows], rtol=1e-13, atol=1e-13 * np.abs(y).max())
+
+
+def test_blocks_are_continuous_at_the_poles():
+    """As the translation vector approaches the z axis (where phi is
+    undefined) the blocks converge to the on-axis block, at first order in the
+    offset: sin(theta) enters as rho / |d| and no cos -> sin cancellation."""
+    k = 2.0 * np.pi / 550.0
+    for zsign in (1.0, -1.0):
+        axis = translation.coupling_blocks(3, k, np.array([[0.0, 0.0, zsign * 400.0]]), np.zeros((1, 3)))[0]
+        scale = np.abs(axis).max()
+        errs = []
+        for eps in (1e-2, 1e-4, 1e-6):
+            for phi in (0.0, 1.0, 2.5):
+                d = np.array([[eps * np.cos(phi), eps * np.sin(phi), zsign * 400.0]])
+                W = translation.coupling_blocks(3, k, d, np.zeros((1, 3)))[0]
+                errs.append(np.abs(W - axis).max() / scale)
+        # offsets two decades apart: the deviation falls by the same factor
+        # (first order, no precision floor down to 1e-6 nm)
+        e = np.array(errs).reshape(3, 3).max(axis=1)
+        assert e[0] < 1e-4
+        assert abs(e[1] / e[0] - 1e-2) < 1e-4 and abs(e[2] / e[1] - 1e-2) < 1e-4
