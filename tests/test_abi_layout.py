@@ -44,3 +44,29 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert ctypes.sizeof(cls) == layout[(name, "size")], name
         for field, _ in cls._fields_:
             assert getattr(cls, field).offset == layout[(name, field)], (name, field)
+
+
+def _prototypes():
+    import re
+    src = open(os.path.join(ROOT, "include", "celes.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][A-Za-z0-9_ \*]*?)\b(celes_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        ret, name, params = m.group(1).strip(), m.group(2), " ".join(m.group(3).split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        protos[name] = (ret, n)
+    return protos
+
+
+def test_binding_signatures_match_the_prototypes():
+    protos = _prototypes()
+    assert len(protos) > 30
+    for name, res, args in binding.SIGNATURES:
+        assert name in protos, name
+        ret, n = protos[name]
+        assert len(args) == n, (name, len(args), n)
+        if ret == "void":
+            assert res is None, name
+        elif ret == "int":
+            assert res is ctypes.c_int, name
