@@ -245,8 +245,8 @@ int auto_chunks(const celes_ctx* c, int precision) {
   // about eight waves of resident CTAs: the last, partly filled wave then
   // idles the GPU for a small fraction of the launch (measured: 12.7 ms at
   // eight waves vs 13.7 ms at four, lmax 4, N = 10 000)
-  const int slots = rtr ? coupling_rtr_slots(c->L, precision) : 152 * 2;
-  const int64_t target = 8LL * (slots > 0 ? slots : 304);
+  const int slots = rtr ? coupling_rtr_slots(c->L, precision) : 2 * device_sms();
+  const int64_t target = 8LL * (slots > 0 ? slots : 2 * device_sms());
   int64_t ch = (target + rb - 1) / rb;
   const int64_t max_by_src = std::max<int64_t>(1, c->N / 64);
   ch = std::min<int64_t>(ch, max_by_src);

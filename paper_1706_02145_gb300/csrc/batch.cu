@@ -384,7 +384,8 @@ namespace {
 
 inline unsigned flat_blocks(long long n) {
   const long long b = (n + 255) / 256;
-  return static_cast<unsigned>(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+  const long long cap = 16LL * celes::device_sms();
+  return static_cast<unsigned>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 // descriptors of the operator y = x - T W x for flat vectors in/out (device

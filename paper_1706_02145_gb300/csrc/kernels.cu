@@ -73,7 +73,8 @@ cudaError_t launch_coupling_epilogue(int64_t N, int L, int chunks, const void* p
   const int64_t total = N * L * (L + 2);
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
-  const int grid = static_cast<int>(blocks < 152 * 32 ? blocks : 152 * 32);
+  const int64_t cap = 32LL * device_sms();
+  const int grid = static_cast<int>(blocks < cap ? blocks : cap);
   coupling_epilogue_kernel<R><<<grid > 0 ? grid : 1, threads, 0, st>>>(
       N, L, chunks, static_cast<const Pair2<R>*>(partial), static_cast<const Pair2<R>*>(x),
       static_cast<const Pair2<R>*>(tq), static_cast<Pair2<R>*>(y), mode);
@@ -348,9 +349,22 @@ __global__ void reduce_partials_kernel(int nblocks, int nv, const double* __rest
   }
 }
 
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n == 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
 int vec_dot_blocks(int64_t n) {
   const int64_t b = (n + kVecThreads - 1) / kVecThreads;
-  return static_cast<int>(b < 4 * 152 ? (b > 0 ? b : 1) : 4 * 152);
+  const int64_t cap = 4LL * device_sms();
+  return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 template <typename R>
@@ -411,7 +425,8 @@ __global__ void multi_combine_kernel(int64_t n, int nv, const Pair2<R>* __restri
 
 static int vec_grid(int64_t n) {
   const int64_t b = (n + kVecThreads - 1) / kVecThreads;
-  return static_cast<int>(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+  const int64_t cap = 16LL * device_sms();
+  return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 template <typename R>

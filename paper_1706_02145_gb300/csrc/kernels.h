@@ -76,6 +76,8 @@ cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, do
                                  const double* weights, double* a, cudaStream_t st);
 
 int vec_dot_blocks(int64_t n);
+// streaming multiprocessors of the current device (queried once per device)
+int device_sms();
 template <typename R>
 cudaError_t launch_multi_dotc(int64_t n, int nv, const void* V, int64_t ldv, const void* w, double* partial,
                               double* out, cudaStream_t st);

@@ -329,7 +329,8 @@ __global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ a, float
 }
 cudaError_t launch_f64_to_f32(int64_t n, const double* a, float* b, cudaStream_t st) {
   const int64_t blocks = (n + 255) / 256;
-  f64_to_f32_kernel<<<static_cast<unsigned>(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16), 256, 0, st>>>(
+  const int64_t cap = 16LL * device_sms();
+  f64_to_f32_kernel<<<static_cast<unsigned>(blocks < cap ? (blocks > 0 ? blocks : 1) : cap), 256, 0, st>>>(
       n, a, b);
   note_launch();
   return cudaGetLastError();
