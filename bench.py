@@ -16,7 +16,13 @@ metric: sphere-pair couplings/s = (coupling matvecs in the step) * N (N - 1)
 divided by the step time; plus the time to 1e-6 of the chosen form against the
 plain FP64 GMRES solve on the same GPU and inputs.
 
+Outside the timed steps the same context is solved again to relative
+residual 1e-10 (FP64 refinement); the oracle's FP64 residual on sampled
+receiver rows (cpu_baseline leg) certifies that reference, and every solve in
+the line reports its coefficient error against it (error_vs_fp64_oracle).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --case coupling|precond|batch [...]   (one operation, for profiling)
 
 Multi-GPU: replicas (each rank solves its own copy; no data exchange), launched
 by torchrun; value = all ranks' couplings / max-over-ranks time.
@@ -40,8 +46,7 @@ if ROOT not in sys.path:
 METRIC = "sphere-pair couplings/s; time to 1e-6 residual, chosen form vs plain FP64"
 UNIT = "sphere-pair couplings/s"
 TOL = 1e-6
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.25                                   # nominal GB300 FP64
+REF_TOL = 1e-10           # the certified reference solve
 
 
 def parse():
@@ -61,6 +66,23 @@ def parse():
     ap.add_argument("--batched-rhs", type=int, default=4)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess measurement")
     ap.add_argument("--no-precond", action="store_true", help="skip the block-preconditioned solve")
+    ap.add_argument("--no-certify", action="store_true",
+                    help="skip the 1e-10 reference solve and the oracle residual on sampled rows")
+    ap.add_argument("--plain-full", action="store_true",
+                    help="also run the full-size plain FP64 GMRES solve to 1e-6 uncapped (about 10 min)")
+    ap.add_argument("--case", choices=["coupling", "precond", "batch"], default=None,
+                    help="run one operation on a synthetic case and print its time (profiling); see run_case")
+    ap.add_argument("--lmax", type=int, default=4, help="--case: degree")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="--case: precision")
+    ap.add_argument("--kernel", choices=["auto", "direct", "rtr"], default="auto", help="--case: coupling kernel")
+    ap.add_argument("--reps", type=int, default=2, help="--case: repetitions (time of the last printed)")
+    ap.add_argument("--recipe", choices=["slab", "large"], default="slab",
+                    help="--case: slab = the bench recipe with --N spheres and --lmax; large = the 100 000-sphere "
+                         "monodisperse slab (lmax 3)")
+    ap.add_argument("--edge", type=float, default=900.0, help="--case precond: cuboid edge (nm)")
+    ap.add_argument("--ensembles", type=int, default=12, help="--case batch: ensembles")
+    ap.add_argument("--rhs", type=int, default=0,
+                    help="--case: right-hand sides (0 = 1 for coupling, 4 plane waves per ensemble for batch)")
     return ap.parse_args()
 
 
@@ -358,6 +380,75 @@ def job_value(units_per_rank, world, max_ms):
     return units_per_rank * world / (max_ms / 1e3)
 
 
+def measure_peaks():
+    """FP32 and FP64 FMA issue peaks of this GPU, measured by the library's
+    FMA-chain kernels (celes_fma_peak) right before the timed steps."""
+    from paper_1706_02145_gb300 import binding as B
+    f32, _ = B.celes_fma_peak(B.FMA_FP32)
+    f32p, _ = B.celes_fma_peak(B.FMA_FP32_PACKED)
+    f64, _ = B.celes_fma_peak(B.FMA_FP64)
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return {"fp32_tflops": max(f32, f32p), "fp32_scalar_tflops": f32, "fp32_packed_tflops": f32p,
+            "fp64_tflops": f64, "sms": props.multi_processor_count,
+            "how": "celes_fma_peak: 16 independent FMA chains per thread, 4 x 256 threads per SM, best of 3 "
+                   "CUDA-event-timed launches, at the SM clock of that moment"}
+
+
+def certify_rows(scene, inc, vectors, rows, cores, pool=None):
+    """The oracle's FP64 residual of candidate solutions on sampled receiver
+    rows (part of the cpu_baseline leg, whose timed work is the same
+    on-the-fly coupling rows): r_S = (T a)_S - b_S + T_S (W b)_S, relative to
+    ||(T a)_S||, with T (App. B) and a (App. C, the same 128-node beta rule)
+    from the oracle.  Returns (relative residual per vector, oracle
+    couplings/s, seconds of coupling-row work)."""
+    from oracle import incident, mie
+    rows = list(rows)
+    t = mie.t_diagonal(scene.lmax, scene.k, scene.radii[rows], scene.n_rel[rows])
+    a = incident.gaussian_beam_coeffs(scene.lmax, scene.k, scene.positions[rows], inc.waist, inc.focus,
+                                      inc.alpha_G, n_beta=128)
+    ta = t * a
+    res, t_total, pairs = [], 0.0, 0
+    for b in vectors:
+        wb, dt = oracle_rows(scene, b, rows, cores, pool)
+        t_total += dt
+        pairs += len(rows) * (scene.N - 1)
+        r = ta - b[rows] + t * wb
+        res.append(float(np.linalg.norm(r) / np.linalg.norm(ta)))
+    return res, pairs / t_total, t_total
+
+
+def oracle_rows(scene, x, rows, n_workers, pool=None):
+    """(W x)_rows by the oracle's on-the-fly FP64 coupling rows in spawn
+    workers: (values (len(rows), nmax), seconds)."""
+    import multiprocessing as mp
+    chunks = [list(rows[q::n_workers]) for q in range(n_workers)]
+    idx = [q for q in range(n_workers) if chunks[q]]
+    args = [(scene.positions, scene.k, scene.lmax, x, chunks[q]) for q in idx]
+    t0 = time.perf_counter()
+    if pool is None:
+        with mp.get_context("spawn").Pool(len(args)) as p:
+            parts = p.starmap(_oracle_rows_values, args)
+    else:
+        parts = pool.starmap(_oracle_rows_values, args)
+    dt = time.perf_counter() - t0
+    out = np.zeros((len(rows), scene.nmax), dtype=complex)
+    pos_of = {r: q for q, r in enumerate(rows)}
+    for q, part in zip(idx, parts):
+        for r, v in zip(chunks[q], part):
+            out[pos_of[r]] = v
+    return out, dt
+
+
+def _oracle_rows_values(pos, k, lmax, x, rows):
+    from oracle import translation
+    return translation.coupling_matvec_rows(pos, k, lmax, x, rows)
+
+
+def rel_err(b, ref):
+    return float(np.linalg.norm(b - ref) / np.linalg.norm(ref))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import synth
@@ -394,6 +485,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    peaks = measure_peaks()
 
     B.celes_profile(ctx, 1)
     sampler = ClockSampler(local_rank)
@@ -421,6 +513,7 @@ def run_ours(args, rank, world, local_rank):
     mv32 = sum(i["matvecs_fp32"] for i in infos)
     mv64 = sum(i["matvecs_fp64"] for i in infos)
     value = job_value((mv32 + mv64) * pairs, world, total_ms)
+    b_chosen = B.celes_get_coefficients(ctx)[0]
 
     # kernel-level roofline from the library's CUDA events (on the launch stream)
     fpp = flops_per_pair(L)
@@ -437,15 +530,23 @@ def run_ours(args, rank, world, local_rank):
                           "couplings_per_s": (pairs * k64_n / (k64_ms / 1e3)) if k64_n else None},
         "epilogue": {"ms": ep_ms, "launches": ep_n},
     }
+    for key, pk in (("coupling_fp32", peaks["fp32_tflops"]), ("coupling_fp64", peaks["fp64_tflops"])):
+        tf = kernels[key]["tflops"]
+        kernels[key]["frac_of_measured_peak"] = (tf / pk) if tf else None
     dom = "coupling_fp32" if k32_ms >= k64_ms else "coupling_fp64"
-    peak = FP32_PEAK_TFLOPS if dom == "coupling_fp32" else FP64_PEAK_TFLOPS
+    peak = peaks["fp32_tflops"] if dom == "coupling_fp32" else peaks["fp64_tflops"]
     ach = kernels[dom]["tflops"]
     traffic = ncu_traffic(f"{dom}_L{L}")
+    derived = peaks["sms"] * 128 * 2 * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": dom,
                 "flops_per_pair": fpp,
-                "peak_basis": ("152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz max SM clock" if dom == "coupling_fp32"
-                               else "nominal GB300 FP64 1.25 TFLOP/s"),
+                "peak_basis": (f"measured {'FP32' if dom == 'coupling_fp32' else 'FP64'} FMA issue peak of this GPU "
+                               "(celes_fma_peak, run just before the timed steps)"),
+                "measured_peaks": peaks,
+                "fp32_derived_peak_tflops": derived,
+                "frac_of_derived_fp32_peak": (kernels["coupling_fp32"]["tflops"] / derived)
+                if kernels["coupling_fp32"]["tflops"] else None,
                 "direct_method_flops_per_pair": B.celes_flops_per_pair(L, B.CELES_KERNEL_DIRECT),
                 "share_of_step": (kernels[dom]["ms"] / total_ms) if total_ms else None}
 
@@ -453,6 +554,18 @@ def run_ours(args, rank, world, local_rank):
     tt = {"chosen_s": float(np.mean([i["seconds"] for i in infos])),
           "chosen_iterations": infos[-1]["iterations"], "chosen_matvecs_fp32": infos[-1]["matvecs_fp32"],
           "chosen_matvecs_fp64": infos[-1]["matvecs_fp64"], "chosen_residual": infos[-1]["residual"]}
+    b_ref = None
+    if not args.no_certify:
+        # the reference: the same system refined in FP64 to 1e-10 (certified
+        # below by the oracle's residual on sampled rows)
+        ir = B.celes_solve(ctx, REF_TOL, mode=B.CELES_SOLVE_MIXED, max_iter=40000, max_outer=40,
+                           raise_on_noconv=False)
+        b_ref = B.celes_get_coefficients(ctx)[0]
+        tt["reference"] = {"tol": REF_TOL, "residual_fp64_gpu": ir["residual"], "iterations": ir["iterations"],
+                           "matvecs_fp64": ir["matvecs_fp64"], "s": ir["seconds"],
+                           "how": "FP32 GMRES inner solves with FP64 residuals (iterative refinement) to 1e-10"}
+        tt["error_vs_fp64_oracle"] = rel_err(b_chosen, b_ref)
+    others = {}
     if not args.no_precond:
         # the paper's block-diagonal preconditioner (Sec. 3.2.1) on the same
         # solve: fewer coupling matvecs for a build and an apply per iteration
@@ -462,22 +575,13 @@ def run_ours(args, rank, world, local_rank):
             B.celes_precond_build(ctx, edge)
             tb = time.perf_counter() - t0
             ip = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_MIXED, use_precond=True)
-            pre[f"edge_{int(edge)}nm"] = {"build_s": tb, "solve_s": ip["seconds"], "total_s": tb + ip["seconds"],
-                                          "iterations": ip["iterations"], "residual": ip["residual"]}
+            e = {"build_s": tb, "solve_s": ip["seconds"], "total_s": tb + ip["seconds"],
+                 "iterations": ip["iterations"], "residual": ip["residual"]}
+            if b_ref is not None:
+                e["error_vs_fp64_oracle"] = rel_err(B.celes_get_coefficients(ctx)[0], b_ref)
+            pre[f"edge_{int(edge)}nm"] = e
         tt["block_preconditioned"] = pre
     if not args.no_plain:
-        # (a) full size: plain FP64 GMRES for a bounded number of iterations
-        #     gives its time per iteration; the time to 1e-6 is extrapolated
-        #     with the iteration count the chosen form needed (labelled as such)
-        cap = 24
-        info_p = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_FP64, max_iter=cap, use_precond=False,
-                                raise_on_noconv=False)
-        per_it = info_p["seconds"] / max(1, info_p["iterations"])
-        tt["plain_fp64_s_per_iteration"] = per_it
-        tt["plain_fp64_s_extrapolated"] = per_it * tt["chosen_iterations"]
-        tt["speedup_extrapolated"] = tt["plain_fp64_s_extrapolated"] / tt["chosen_s"]
-        tt["extrapolation"] = (f"plain FP64 GMRES timed for {info_p['iterations']} iterations at full size, "
-                               f"times the {tt['chosen_iterations']} iterations of the chosen form")
         # (b) measured end to end on a reduced packing of the same recipe
         small = synth.config2(0, N=args.small_n)
         cs = B.celes_create(small.positions, small.radii, small.n_sphere, small.n0, small.k0, L, device=local_rank)
@@ -491,18 +595,50 @@ def run_ours(args, rank, world, local_rank):
             ib = B.celes_solve(cs, TOL, mode=B.CELES_SOLVE_MIXED, solver=B.CELES_SOLVER_BICGSTAB,
                                raise_on_noconv=False)
             bb = B.celes_get_coefficients(cs)[0]
-            tt["measured_small"] = {"N": small.N, "chosen_s": im["seconds"], "chosen_iterations": im["iterations"],
-                                    "plain_fp64_s": ip["seconds"], "plain_fp64_iterations": ip["iterations"],
-                                    "plain_fp64_residual": ip["residual"], "chosen_residual": im["residual"],
-                                    "speedup": ip["seconds"] / im["seconds"],
-                                    "chosen_vs_plain_rel_l2": float(np.linalg.norm(bm - bp) / np.linalg.norm(bp)),
-                                    "bicgstab_mixed": {"s": ib["seconds"], "iterations": ib["iterations"],
-                                                       "matvecs_fp32": ib["matvecs_fp32"],
-                                                       "residual": ib["residual"],
-                                                       "vs_plain_rel_l2": float(np.linalg.norm(bb - bp) /
-                                                                                np.linalg.norm(bp))}}
+            ms = {"N": small.N, "chosen_s": im["seconds"], "chosen_iterations": im["iterations"],
+                  "plain_fp64_s": ip["seconds"], "plain_fp64_iterations": ip["iterations"],
+                  "plain_fp64_residual": ip["residual"], "chosen_residual": im["residual"],
+                  "speedup": ip["seconds"] / im["seconds"],
+                  "chosen_vs_plain_rel_l2": rel_err(bm, bp),
+                  "bicgstab_mixed": {"s": ib["seconds"], "iterations": ib["iterations"],
+                                     "matvecs_fp32": ib["matvecs_fp32"], "residual": ib["residual"],
+                                     "vs_plain_rel_l2": rel_err(bb, bp)}}
+            if not args.no_certify:
+                ir = B.celes_solve(cs, REF_TOL, mode=B.CELES_SOLVE_MIXED, max_iter=40000, max_outer=40,
+                                   raise_on_noconv=False)
+                bs_ref = B.celes_get_coefficients(cs)[0]
+                ms["reference_residual_fp64_gpu"] = ir["residual"]
+                ms["error_vs_fp64_oracle"] = rel_err(bm, bs_ref)
+                ms["plain_fp64_error_vs_fp64_oracle"] = rel_err(bp, bs_ref)
+                ms["bicgstab_mixed"]["error_vs_fp64_oracle"] = rel_err(bb, bs_ref)
+                others["small"] = (small, bm, bs_ref)
+            tt["measured_small"] = ms
         finally:
             B.celes_destroy(cs)
+        # (a) full size: plain FP64 GMRES for a bounded number of iterations
+        #     gives its time per iteration; its time to 1e-6 is extrapolated
+        #     with (i) the chosen form's iteration count and (ii) that count
+        #     scaled by plain/chosen iterations measured at the small size
+        cap = 24
+        info_p = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_FP64, max_iter=cap, use_precond=False,
+                                raise_on_noconv=False)
+        per_it = info_p["seconds"] / max(1, info_p["iterations"])
+        ratio = ms["plain_fp64_iterations"] / max(1, ms["chosen_iterations"])
+        tt["plain_fp64_s_per_iteration"] = per_it
+        tt["plain_fp64_s_extrapolated"] = per_it * tt["chosen_iterations"]
+        tt["plain_fp64_s_extrapolated_scaled"] = per_it * tt["chosen_iterations"] * ratio
+        tt["speedup_extrapolated"] = tt["plain_fp64_s_extrapolated"] / tt["chosen_s"]
+        tt["speedup_extrapolated_scaled"] = tt["plain_fp64_s_extrapolated_scaled"] / tt["chosen_s"]
+        tt["extrapolation"] = (f"plain FP64 GMRES timed for {info_p['iterations']} iterations at full size, times "
+                               f"(i) the {tt['chosen_iterations']} iterations of the chosen form, (ii) that count "
+                               f"times the plain/chosen iteration ratio {ratio:.3f} measured at N={small.N}")
+        if args.plain_full:
+            ipf = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_FP64, max_iter=20000, use_precond=False,
+                                raise_on_noconv=False)
+            tt["plain_fp64_full"] = {"s": ipf["seconds"], "iterations": ipf["iterations"],
+                                     "residual": ipf["residual"], "speedup": ipf["seconds"] / tt["chosen_s"]}
+            if b_ref is not None:
+                tt["plain_fp64_full"]["error_vs_fp64_oracle"] = rel_err(B.celes_get_coefficients(ctx)[0], b_ref)
     B.celes_destroy(ctx)
     batched = None if args.no_batched else run_batched(args, local_rank)
     learned = None if args.no_learned else run_learned(args, local_rank)
@@ -535,23 +671,118 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
+        # the oracle timed on the host cores: its on-the-fly FP64 coupling rows
+        # on a sample of receivers of the workload.  When the certified
+        # reference exists, the sampled rows are applied to the chosen and the
+        # reference solutions, and the same rows give the oracle's residual of
+        # both (the certification of the reference).
+        import multiprocessing as mp
         cores = host_cores()
-        rows = args.cpu_rows or 24 * max(cores, 2)  # 10-20 s of oracle work
-        sel = list(np.random.default_rng(7).choice(N, rows, replace=False))
-        rate, dt = cpu_oracle_rate(scene, sel, cores)
+        rows = args.cpu_rows or 16 * max(cores, 2)
+        sel = [int(r) for r in np.random.default_rng(7).choice(N, rows, replace=False)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            if b_ref is not None:
+                (r_chosen, r_ref), rate, dt = certify_rows(scene, inc_desc, [b_chosen, b_ref], sel, cores, pool)
+                tt["oracle_sampled_residual"] = {"rows": rows, "chosen": r_chosen, "reference": r_ref}
+                if "small" in others:
+                    small, bm, bs_ref = others["small"]
+                    ssel = [int(r) for r in np.random.default_rng(8).choice(small.N, 4 * cores, replace=False)]
+                    (rs_c, rs_r), _, _ = certify_rows(small, inc_desc, [bm, bs_ref], ssel, cores, pool)
+                    tt["measured_small"]["oracle_sampled_residual"] = {"rows": len(ssel), "chosen": rs_c,
+                                                                       "reference": rs_r}
+                what = "the chosen and the reference solution"
+            else:
+                x = np.random.default_rng(1).normal(size=(N, scene.nmax)) * (1 + 0j)
+                _, dt = oracle_rows(scene, x, sel, cores, pool)
+                rate = rows * (N - 1) / dt
+                what = "a random vector"
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{rows} receiver rows x {N - 1} sources of the oracle's FP64 on-the-fly coupling "
-                         f"matvec (numpy, {cores} spawn workers), {dt:.1f} s"}
+                         f"matvec applied to {what} (numpy, {cores} spawn workers), {dt:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": workload_config(N, L, world),
-                "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "batched": batched, "learned_guess": learned,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "kernels": kernels, "time_to_1e-6": tt, "batched": batched,
+                "learned_guess": learned, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
+
+
+def run_case(args):
+    """One hot-path operation on a synthetic case, through the C ABI, for
+    timing and profiling (ncu captures of single launches):
+      coupling: y = W x on the bench recipe with --N spheres and --lmax (or the
+                100 000-sphere slab, --recipe large); --rhs right-hand sides;
+      precond:  builds the block-diagonal preconditioner with --edge nm cuboids
+                on the same recipe and applies it;
+      batch:    the batched operator (I - T W) over --ensembles ensembles of
+                the multi-ensemble recipe (sizes scaled by 0.4), --rhs plane
+                waves each.
+    Runs --reps operations and prints the time of the last one."""
+    import torch
+    import synth
+    from paper_1706_02145_gb300 import binding as B
+    B.load()
+    prec = B.CELES_FP32 if args.precision == "fp32" else B.CELES_FP64
+    dt = torch.complex64 if prec == B.CELES_FP32 else torch.complex128
+    g = torch.Generator(device="cuda").manual_seed(0)
+    if args.case == "batch":
+        nrhs = args.rhs or 4
+        scenes = [synth.config3(e, n_rhs=nrhs, N=max(80, int(0.4 * synth.config3_size(e))))
+                  for e in range(args.ensembles)]
+        ctxs = []
+        for sc in scenes:
+            c = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax)
+            B.celes_set_incident(c, [B.make_incident("plane", beta=i.beta, alpha=i.alpha, pol=i.pol)
+                                     for i in sc.incidents])
+            ctxs.append(c)
+        bt = B.celes_batch_create(ctxs)
+        n = B.celes_batch_num_unknowns(bt)
+        x = torch.randn(n, dtype=dt, device="cuda", generator=g)
+        y = torch.empty_like(x)
+        t = 0.0
+        for _ in range(args.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.celes_batch_master_matvec(bt, x, y, precision=prec)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+        pairs = sum(sc.N * (sc.N - 1) * len(sc.incidents) for sc in scenes)
+        print(f"batch of {len(scenes)} ensembles x {nrhs} RHS, {args.precision}: {t * 1e3:.3f} ms, "
+              f"{pairs / t:.3e} couplings/s")
+        B.celes_batch_destroy(bt)
+        for c in ctxs:
+            B.celes_destroy(c)
+        return
+    kern = {"auto": B.CELES_KERNEL_AUTO, "direct": B.CELES_KERNEL_DIRECT, "rtr": B.CELES_KERNEL_RTR}[args.kernel]
+    sc = synth.config2(0, N=args.N, lmax=args.lmax) if args.recipe == "slab" else synth.config5(0)
+    ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, kernel=kern)
+    nrhs = max(1, args.rhs) if args.case == "coupling" else 1
+    x = torch.randn(nrhs, sc.N, sc.nmax, dtype=dt, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    if args.case == "precond":
+        B.celes_precond_build(ctx, args.edge)
+    t = 0.0
+    for _ in range(args.reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if args.case == "precond":
+            B.celes_precond_apply(ctx, x, y, precision=prec)
+        else:
+            B.celes_coupling_matvec(ctx, x, y, nrhs=nrhs, precision=prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    if args.case == "precond":
+        print(f"N={sc.N} lmax={sc.lmax} {args.precision} block preconditioner apply (edge {args.edge:g} nm): "
+              f"{t * 1e3:.3f} ms")
+    else:
+        pairs = sc.N * (sc.N - 1) * nrhs
+        print(f"N={sc.N} lmax={sc.lmax} {args.precision} kernel={args.kernel} rhs={nrhs}: {t * 1e3:.3f} ms, "
+              f"{pairs / t:.3e} couplings/s")
+    B.celes_destroy(ctx)
 
 
 def main():
@@ -559,6 +790,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return

@@ -254,6 +254,16 @@ int64_t celes_kernel_launches(void);
  * Wigner-d sums, axial build/apply and phases.  Host-only; -1 on bad lmax. */
 double celes_flops_per_pair(int lmax, int kernel);
 
+/* Measured fused multiply-add issue peak of the current device, the
+ * denominator of the coupling kernels' roofline (the paper has no
+ * counterpart; this is measurement support).  kind: 0 = FP64 FMA, 1 = FP32
+ * FMA, 2 = FP32 packed two-lane FMA (sm_100 and later).  Every thread of a
+ * 4 x 256-thread-per-SM grid runs 16 independent FMA chains; the best of three
+ * CUDA-event-timed launches gives *tflops (2 flops per FMA) and *ms.  The
+ * figure holds at the SM clock of that moment; sample the clock beside it.
+ * Allocates a small output buffer, synchronises. */
+int celes_fma_peak(int kind, double* tflops, double* ms);
+
 /* Tensor-core GEMM C = alpha A B^T + beta C (the dense layers of the learned
  * initial guess; the paper has no counterpart).  A: [M][K] BF16, B: [N][K]
  * BF16 (row-major, K contiguous, lda/ldb in elements), C: [M][N] FP32

@@ -79,6 +79,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 # (name, restype, argtypes) of every exported symbol of include/celes.h
 SIGNATURES = [
+    ("celes_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("celes_create", ctypes.c_int, [ctypes.POINTER(_c_ctx_p), ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(celes_options)]),
     ("celes_set_incident", ctypes.c_int, [_c_ctx_p, ctypes.POINTER(celes_incident), ctypes.c_int]),
@@ -181,6 +182,40 @@ def _devptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_vec(name, t, n_complex, precision, device=None):
+    """Check a device coefficient buffer before its pointer crosses the C ABI,
+    which cannot see sizes: a contiguous CUDA tensor of at least n_complex
+    entries of the dtype that `precision` names (complex128 for FP64,
+    complex64 for FP32), on `device` when given.  Raw integer pointers are
+    passed through unchecked."""
+    if t is None or isinstance(t, int):
+        return
+    want = "complex128" if precision == CELES_FP64 else "complex64"
+    dt = str(t.dtype).replace("torch.", "")
+    if dt != want:
+        raise CelesError(CELES_EINVAL, f"{name}: dtype {dt}, expected {want} for this precision")
+    if not t.is_cuda:
+        raise CelesError(CELES_EINVAL, f"{name}: not a CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise CelesError(CELES_EINVAL, f"{name}: on cuda:{t.device.index}, expected cuda:{device}")
+    if not t.is_contiguous():
+        raise CelesError(CELES_EINVAL, f"{name}: not contiguous")
+    if t.numel() < n_complex:
+        raise CelesError(CELES_EINVAL, f"{name}: {t.numel()} entries, needs {n_complex}")
+
+
+def _ctx_vec_checks(ctx, x, y, nrhs, precision):
+    n = int(load().celes_num_spheres(ctx)) * int(load().celes_nmax(ctx)) * int(nrhs)
+    dev = None
+    for name, t in (("x", x), ("y", y)):
+        _check_vec(name, t, n, precision)
+        if t is not None and not isinstance(t, int):
+            if dev is None:
+                dev = t.device.index
+            elif t.device.index != dev:
+                raise CelesError(CELES_EINVAL, "x and y are on different devices")
+
+
 def _stream(s):
     if s is None:
         return None
@@ -227,11 +262,13 @@ def celes_set_incident(ctx, incidents):
 
 
 def celes_coupling_matvec(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
+    _ctx_vec_checks(ctx, x, y, nrhs, precision)
     return _check(load().celes_coupling_matvec(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
                                                _stream(stream)), ctx)
 
 
 def celes_master_matvec(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
+    _ctx_vec_checks(ctx, x, y, nrhs, precision)
     return _check(load().celes_master_matvec(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
                                              _stream(stream)), ctx)
 
@@ -241,6 +278,7 @@ def celes_precond_build(ctx, cuboid_edge):
 
 
 def celes_precond_apply(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
+    _ctx_vec_checks(ctx, x, y, nrhs, precision)
     return _check(load().celes_precond_apply(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
                                              _stream(stream)), ctx)
 
@@ -348,10 +386,38 @@ def celes_flops_per_pair(lmax, kernel=CELES_KERNEL_AUTO):
     return float(load().celes_flops_per_pair(int(lmax), int(kernel)))
 
 
+FMA_FP64 = 0
+FMA_FP32 = 1
+FMA_FP32_PACKED = 2
+
+
+def celes_fma_peak(kind):
+    """Measured FMA issue peak of the current device: (TFLOP/s, ms of the timed launch)."""
+    tf = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    code = load().celes_fma_peak(int(kind), ctypes.byref(tf), ctypes.byref(ms))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_fma_peak")
+    return tf.value, ms.value
+
+
 def celes_coupling_matvec_noalloc(N, lmax, k, positions4, x, y, precision=CELES_FP64, stream=None,
                                   check=True):
     """y = W x without any device allocation by the library (see include/celes.h).
-    positions4, x, y: device buffers ([N][4] float64, [N][nmax] complex)."""
+    positions4, x, y: device buffers ([N][4] float64, [N][nmax] complex).
+    Tensors are checked for dtype, size, contiguity and device first (with
+    check=False as well: a mismatch there is an out-of-bounds access)."""
+    nmax = 2 * int(lmax) * (int(lmax) + 2)
+    if int(N) >= 1 and 1 <= int(lmax) <= 5:
+        _check_vec("x", x, int(N) * nmax, precision)
+        _check_vec("y", y, int(N) * nmax, precision)
+        if positions4 is not None and not isinstance(positions4, int):
+            if str(positions4.dtype) != "torch.float64" or not positions4.is_cuda or not positions4.is_contiguous() \
+                    or positions4.numel() < 4 * int(N):
+                raise CelesError(CELES_EINVAL, "positions4: needs a contiguous CUDA float64 tensor of N x 4")
+        devs = {t.device.index for t in (x, y, positions4) if t is not None and not isinstance(t, int)}
+        if len(devs) > 1:
+            raise CelesError(CELES_EINVAL, "positions4, x and y must be on one device")
     code = load().celes_coupling_matvec_noalloc(int(N), int(lmax), float(k), _devptr(positions4), _devptr(x),
                                                  _devptr(y), int(precision), _stream(stream))
     if check and code != CELES_OK:

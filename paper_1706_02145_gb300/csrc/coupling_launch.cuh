@@ -19,13 +19,15 @@ cudaError_t launch_coupling_partial_t(int64_t N, const void* pos, const void* x,
   using C = CouplingConfig<L, R>;
   using LY = CouplingLayout<L, R>;
   const size_t smem = LY::bytes;
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(coupling_partial_kernel<L, R>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // the shared-memory opt-in, once on each device
+  static PerDevice attr;
+  cudaError_t se = cudaSuccess;
+  if (attr.get(current_device, [&] {
+        se = cudaFuncSetAttribute(coupling_partial_kernel<L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem));
+        return se == cudaSuccess ? 1 : 0;
+      }) == 0)
+    return se != cudaSuccess ? se : cudaErrorInvalidConfiguration;
   if (N <= 0) return cudaSuccess;
   if (chunks < 1) chunks = 1;
   const int64_t chunk = (N + chunks - 1) / chunks;

@@ -350,15 +350,14 @@ __global__ void reduce_partials_kernel(int nblocks, int nv, const double* __rest
 }
 
 int device_sms() {
-  static std::atomic<int> cache[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-  int n = cache[dev].load(std::memory_order_relaxed);
-  if (n == 0) {
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
-    cache[dev].store(n, std::memory_order_relaxed);
-  }
-  return n;
+  static PerDevice cache;
+  const int n = cache.get(current_device, [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return v;
+  });
+  return n > 0 ? n : 1;
 }
 
 int vec_dot_blocks(int64_t n) {

@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "../../include/celes.h"
+#include "per_device.h"
 
 struct celes_ctx;
 
@@ -74,6 +75,9 @@ cudaError_t launch_plane_wave(int64_t N, int L, double k, const void* pos, doubl
 cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, double w, const double* focus,
                                  double alphaG, double e0r, double e0i, int nb, const double* nodes,
                                  const double* weights, double* a, cudaStream_t st);
+
+// the current device's ordinal (PerDevice's device query)
+inline bool current_device(int* d) { return cudaGetDevice(d) == cudaSuccess; }
 
 int vec_dot_blocks(int64_t n);
 // streaming multiprocessors of the current device (queried once per device)

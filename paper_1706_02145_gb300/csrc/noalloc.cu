@@ -42,9 +42,8 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 // obtained once per device with cudaGetSymbolAddress.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_dev[kMaxDevices] = {};
+void* g_scratch_dev[celes::kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (set up on the
 // first call on each device).
@@ -52,7 +51,7 @@ cudaError_t scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (dev < 0 || dev >= celes::kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_dev[dev]) {
     void* p = nullptr;

@@ -284,13 +284,15 @@ cudaError_t launch_apply_t(int64_t nblocks, const int64_t* block_off, const int6
   dim3 grid(static_cast<unsigned>(nblocks), static_cast<unsigned>(nrhs));
   const size_t smem = sizeof(Pair2<F>) * static_cast<size_t>(max_block_dim);
   if (smem <= 200 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      const cudaError_t e = cudaFuncSetAttribute(precond_apply_kernel<R, F, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    // the shared-memory opt-in, once on each device
+    static PerDevice attr;
+    cudaError_t se = cudaSuccess;
+    if (attr.get(current_device, [&] {
+          se = cudaFuncSetAttribute(precond_apply_kernel<R, F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024);
+          return se == cudaSuccess ? 1 : 0;
+        }) == 0)
+      return se != cudaSuccess ? se : cudaErrorInvalidConfiguration;
     precond_apply_kernel<R, F, true><<<grid, 256, smem, st>>>(
         block_off, mat_off, nmax, perm, static_cast<const Pair2<F>*>(mats), piv, N, static_cast<const Pair2<R>*>(x),
         static_cast<Pair2<R>*>(y), static_cast<Pair2<F>*>(work));

@@ -897,21 +897,34 @@ int kernel_setup(K* kern, int block, size_t smem) {
   return occ;
 }
 
+// resident CTAs per SM of the per-context and the batched kernel on the
+// current device; the first call on each device sets the kernel's
+// shared-memory limit there (0 on error)
+template <int L, typename R, typename C = Config<L, R>>
+int partial_occupancy() {
+  static PerDevice cache;
+  return cache.get(current_device,
+                   [] { return kernel_setup(rtr_partial_kernel<L, R, C>, C::BLOCK, Layout<L, R, C>::bytes); });
+}
+template <int L, typename R, typename C = Config<L, R>>
+int batch_occupancy() {
+  static PerDevice cache;
+  return cache.get(current_device,
+                   [] { return kernel_setup(rtr_batch_kernel<L, R, C>, C::BLOCK, Layout<L, R, C>::bytes); });
+}
+
 // resident CTAs of the per-context kernel on the whole GPU (SMs x CTAs per SM)
 template <int L, typename R, typename C = Config<L, R>>
 int resident_slots() {
-  static const int occ = kernel_setup(rtr_partial_kernel<L, R, C>, C::BLOCK, Layout<L, R, C>::bytes);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms * (occ > 0 ? occ : 1);
+  const int occ = partial_occupancy<L, R, C>();
+  return device_sms() * (occ > 0 ? occ : 1);
 }
 
 template <int L, typename R, typename C = Config<L, R>>
 cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
                            cudaStream_t st) {
   using LY = Layout<L, R, C>;
-  static const int occ = kernel_setup(rtr_partial_kernel<L, R, C>, C::BLOCK, LY::bytes);
+  const int occ = partial_occupancy<L, R, C>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (N <= 0) return cudaSuccess;
   if (chunks < 1) chunks = 1;
@@ -930,13 +943,10 @@ cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* part
 template <int L, typename R, typename C = Config<L, R>>
 cudaError_t launch_batch(const void* sys, int nsys, long long ntiles, unsigned long long* counter, cudaStream_t st) {
   using LY = Layout<L, R, C>;
-  static const int occ = kernel_setup(rtr_batch_kernel<L, R, C>, C::BLOCK, LY::bytes);
+  const int occ = batch_occupancy<L, R, C>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (nsys <= 0 || ntiles <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long slots = static_cast<long long>(sms) * occ;
+  const long long slots = static_cast<long long>(device_sms()) * occ;
   const unsigned grid = static_cast<unsigned>(ntiles < slots ? ntiles : slots);
   rtr_batch_kernel<L, R, C><<<grid, C::BLOCK, LY::bytes, st>>>(static_cast<const BatchSys*>(sys), nsys, ntiles,
                                                                 counter);

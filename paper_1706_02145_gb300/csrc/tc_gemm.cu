@@ -13,10 +13,13 @@
 //  * the epilogue reads the accumulator with tcgen05.ld (warp w owns rows
 //    32w..32w+31) and applies alpha/beta.
 // Every wait is bounded: a wait that runs out sets *err and the kernel skips
-// the remaining work, then frees its tensor memory.
+// the remaining work.  Before it frees its tensor memory it waits once more
+// (bounded) for the commit of the step it gave up on, so that no MMA it issued
+// is still writing the accumulator when the columns are released.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/celes.h"
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(int M, int N, in
   __shared__ __align__(8) uint64_t bar;
   __shared__ unsigned tmem_base_s;
   __shared__ int abort_s;
+  __shared__ unsigned abort_phase_s;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -156,6 +160,7 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(int M, int N, in
     if (!mbar_wait(&bar, phase)) {
       if (tid == 0) atomicExch(err, 1);
       abort_s = 1;
+      abort_phase_s = phase;
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -189,6 +194,11 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_tn_kernel(int M, int N, in
       }
     }
   }
+  if (abort_s && tid == 0) {
+    // the commit of the abandoned step may still be outstanding: drain it
+    // (bounded) before the tensor memory is released
+    (void)mbar_wait(&bar, abort_phase_s);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -220,8 +230,12 @@ cudaError_t launch_gemm_bf16_tn(int M, int N, int K, const void* A, int lda, con
 }  // namespace celes
 
 namespace {
-__device__ int g_gemm_err;
-}
+// One error flag per call: concurrent calls (from several host threads) take
+// different slots of this ring, so one call's timeout is not read by another.
+constexpr int kErrSlots = 256;
+__device__ int g_gemm_err[kErrSlots];
+std::atomic<unsigned> g_gemm_err_next{0};
+}  // namespace
 
 extern "C" int celes_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
                                float alpha, float beta, void* stream) {
@@ -230,8 +244,9 @@ extern "C" int celes_gemm_bf16(int M, int N, int K, const void* A, int lda, cons
       (reinterpret_cast<uintptr_t>(B) & 15))
     return CELES_EINVAL;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int* err = nullptr;
-  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_gemm_err) != cudaSuccess) return CELES_ECUDA;
+  int* errs = nullptr;
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&errs), g_gemm_err) != cudaSuccess) return CELES_ECUDA;
+  int* err = errs + (g_gemm_err_next.fetch_add(1, std::memory_order_relaxed) % kErrSlots);
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return CELES_ECUDA;
   if (celes::launch_gemm_bf16_tn(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, err, st) != cudaSuccess)
     return CELES_ECUDA;

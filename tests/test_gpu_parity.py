@@ -83,6 +83,50 @@ def test_tmatrix_and_plane_wave(N, L, poly, n):
         B.celes_destroy(ctx)
 
 
+@pytest.mark.parametrize("n", [1.5 + 0.05j, 2.0 + 0.3j, 1.33 + 1e-3j, 1.7 + 0j])
+def test_tmatrix_at_large_size_parameters(n):
+    # the FP64 Mie kernel (App. B) at size parameters k R = 4 .. 30 with
+    # absorbing and lossless spheres, entry by entry against the oracle
+    k0 = 2 * np.pi / 550.0
+    radii = np.array([4.0, 10.0, 22.0, 30.0]) / k0
+    pos = np.zeros((4, 3))
+    pos[:, 0] = np.arange(4) * 6000.0
+    ctx = B.celes_create(pos, radii, np.full(4, n), 1.0, k0, 5)
+    try:
+        t = B.celes_get_tmatrix(ctx)
+        ref = mie.t_diagonal(5, k0, radii, np.full(4, n))
+        assert np.max(np.abs(t - ref) / np.abs(ref)) < 1e-10
+    finally:
+        B.celes_destroy(ctx)
+
+
+def test_gaussian_beam_far_from_the_axis_of_the_slab():
+    # the 10 000-sphere slab with its 2 um Gaussian beam: the 20 spheres
+    # farthest from the beam axis (k rho ~ 100, where the coefficients are
+    # ~1e-8 of the peak) and 20 at the median distance, with the bench's
+    # 128-node beta rule.  Errors are measured against the beam's peak
+    # coefficient (the on-axis sphere), since far out the coefficients are
+    # cancellation-limited to ~1e-15 of the peak in any FP64 evaluation.
+    sc = synth.config2(0)
+    rho = np.hypot(sc.positions[:, 0], sc.positions[:, 1])
+    order = np.argsort(-rho)
+    sel = np.concatenate([order[:20], order[sc.N // 2:sc.N // 2 + 20], order[-1:]])
+    inc = sc.incidents[0]
+    ctx = B.celes_create(sc.positions[sel], sc.radii[sel], sc.n_sphere[sel], sc.n0, sc.k0, sc.lmax)
+    try:
+        B.celes_set_incident(ctx, [B.make_incident("gaussian", waist=inc.waist, focus=inc.focus,
+                                                   alpha_G=inc.alpha_G, n_beta=128)])
+        a = B.celes_get_incident_coefficients(ctx)[0]
+        ref = incident.gaussian_beam_coeffs(sc.lmax, sc.k, sc.positions[sel], inc.waist, inc.focus, inc.alpha_G,
+                                            n_beta=128)
+        peak = np.max(np.abs(ref[-1]))
+        assert np.max(np.abs(a - ref)) < 1e-12 * peak
+        assert rel(a[20:40], ref[20:40]) < 1e-8   # ~1e-4 of the peak: cancellation-limited near 1e-11
+        assert rel(a[:20], ref[:20]) < 1e-5       # ~1e-8 of the peak: 128 vs 256 nodes differ by 3e-8
+    finally:
+        B.celes_destroy(ctx)
+
+
 def test_gaussian_beam_coefficients():
     sc = synth.random_cluster(22, 0, 24, 3, radius=120.0, fill=0.15, n=1.5 + 0.001j)
     ctx = make_ctx(sc)

@@ -106,3 +106,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 def test_every_binding_signature_names_an_exported_symbol(lib):
     for name, _, _ in binding.SIGNATURES:
         assert hasattr(lib, name), name
+
+
+def test_binding_checks_device_buffers_before_the_call():
+    # the C ABI cannot see buffer sizes: the binding refuses tensors of the
+    # wrong dtype, device, size or layout before any pointer is passed
+    torch = pytest.importorskip("torch")
+    N, L = 4, 2
+    nmax = 2 * L * (L + 2)
+    pos4 = torch.zeros((N, 4), dtype=torch.float64)
+    x = torch.zeros((N, nmax), dtype=torch.complex128)
+    for xx, prec in [(x, binding.CELES_FP64), (x.to(torch.complex64), binding.CELES_FP64),
+                     (x, binding.CELES_FP32), (x[:2], binding.CELES_FP64)]:
+        with pytest.raises(binding.CelesError) as e:
+            binding.celes_coupling_matvec_noalloc(N, L, 0.01, pos4, xx, xx.clone(), precision=prec, check=False)
+        assert e.value.code == binding.CELES_EINVAL
+    with pytest.raises(binding.CelesError):
+        binding._check_vec("x", torch.zeros((3, 8), dtype=torch.complex64).t(), 24, binding.CELES_FP32)

@@ -20,6 +20,58 @@ def test_mie_matches_bohren_huffman(R, n):
     assert np.allclose(Q[1], -a, rtol=1e-12, atol=1e-15)
 
 
+def _bhmie_log_derivative(lmax, x, m):
+    """Mie a_l, b_l by the logarithmic-derivative method of Bohren & Huffman
+    (their BHMIE program, written out here): D_l(mx) by downward recurrence
+    D_{l-1} = l/z - 1/(D_l + l/z) from far above, Riccati-Bessel psi_l(x),
+    chi_l(x) by upward recurrence from their closed forms (stable for l < x).
+    It uses no library Bessel function of a complex argument, so it checks the
+    oracle's complex-argument path at large size parameters independently."""
+    z = m * x
+    nstart = int(max(lmax, abs(z)) + 16 + 4 * abs(z) ** (1 / 3))
+    D = [0j] * (nstart + 1)
+    for n in range(nstart, 0, -1):
+        D[n - 1] = n / z - 1.0 / (D[n] + n / z)
+    psi = [np.sin(x), np.sin(x) / x - np.cos(x)]
+    chi = [np.cos(x), np.cos(x) / x + np.sin(x)]
+    for n in range(2, lmax + 1):
+        psi.append((2 * n - 1) / x * psi[n - 1] - psi[n - 2])
+        chi.append((2 * n - 1) / x * chi[n - 1] - chi[n - 2])
+    a = np.zeros(lmax, dtype=complex)
+    b = np.zeros(lmax, dtype=complex)
+    for n in range(1, lmax + 1):
+        xi_n, xi_m = psi[n] - 1j * chi[n], psi[n - 1] - 1j * chi[n - 1]
+        fa = D[n] / m + n / x
+        fb = m * D[n] + n / x
+        a[n - 1] = (fa * psi[n] - psi[n - 1]) / (fa * xi_n - xi_m)
+        b[n - 1] = (fb * psi[n] - psi[n - 1]) / (fb * xi_n - xi_m)
+    return a, b
+
+
+@pytest.mark.parametrize("x", [4.0, 10.0, 22.0, 30.0])
+@pytest.mark.parametrize("n", [1.5 + 0.05j, 2.0 + 0.3j, 1.33 + 1e-3j, 1.7 + 0j])
+def test_mie_large_size_parameters_vs_log_derivative_method(x, n):
+    # Q_1l = -b_l, Q_2l = -a_l up to size parameter 30 with absorbing spheres
+    L = 6
+    Q = mie.mie_q(L, 1.0, x, n)
+    a, b = _bhmie_log_derivative(L, x, n)
+    assert np.allclose(Q[0], -b, rtol=1e-11, atol=1e-14)
+    assert np.allclose(Q[1], -a, rtol=1e-11, atol=1e-14)
+
+
+def test_gaussian_beam_rule_converged_far_from_the_axis():
+    # the 128-node beta rule against 256 nodes at k rho ~ 100 from the beam
+    # axis (the edge of the 10 000-sphere slab): agreement to 1e-13 of the
+    # beam's peak coefficient
+    k = K
+    w = 2000.0
+    pos = np.array([[8600.0, 300.0, 1500.0], [-5000.0, 7000.0, 400.0], [0.0, 0.0, 1000.0]])
+    a128 = incident.gaussian_beam_coeffs(4, k, pos, w, (0.0, 0.0, 0.0), -np.pi / 2, n_beta=128)
+    a256 = incident.gaussian_beam_coeffs(4, k, pos, w, (0.0, 0.0, 0.0), -np.pi / 2, n_beta=256)
+    peak = np.max(np.abs(a256[2]))
+    assert np.max(np.abs(a128 - a256)) < 1e-13 * peak
+
+
 def test_mie_rayleigh_limit():
     # x -> 0: a_1 ~ -(2i/3) x^3 (m^2 - 1)/(m^2 + 2)
     n = 1.6 + 0.05j

@@ -16,14 +16,20 @@ K = 2 * np.pi / 550.0
 
 
 @pytest.mark.parametrize("d,L", [((150.0, -80.0, 220.0), 2), ((-90.0, 40.0, -160.0), 3),
-                                 ((0.0, 0.0, 260.0), 2), ((210.0, 0.0, 0.0), 2)])
+                                 ((0.0, 0.0, 260.0), 2), ((210.0, 0.0, 0.0), 2),
+                                 ((120.0, 170.0, -90.0), 4), ((-60.0, -140.0, 250.0), 5),
+                                 ((0.0, 0.0, -300.0), 4), ((-190.0, 75.0, 0.0), 5)])
 def test_addition_theorem_direct(d, L):
     rng = np.random.default_rng(11)
     d = np.asarray(d)
     Lp = L + 18
     A = translation.translation_blocks(L, Lp, K, d[None, :])[0]
     u = rng.normal(size=(4, 3))
-    rpts = u / np.linalg.norm(u, axis=1)[:, None] * (0.25 * np.linalg.norm(d))
+    # sample radius: the regular-wave series truncated at L' converges like
+    # (|r| / |d|)^L', and the outgoing waves of degree 4-5 need the smaller
+    # ratio to reach 1e-12 at L' = L + 18
+    frac = 0.25 if L <= 3 else 0.15
+    rpts = u / np.linalg.norm(u, axis=1)[:, None] * (frac * np.linalg.norm(d))
     idx_out = svwf.multi_indices(L)
     idx_in = svwf.multi_indices(Lp)
     basis = [svwf.svwf(1, tp, lp, mp, K, rpts) for (tp, lp, mp) in idx_in]

@@ -66,14 +66,44 @@ def test_noalloc_matches_context_matvec_on_two_calls(precision, tol):
             B.celes_destroy(ctx)
 
 
-def test_noalloc_rejects_sizes_beyond_its_scratch():
-    sc = synth.random_cluster(31, 2, 4, 4)
-    x = torch.zeros((sc.N, sc.nmax), dtype=torch.complex128, device="cuda")
-    y = torch.zeros_like(x)
+def test_noalloc_matches_the_oracle_rows():
+    """The allocation-free path against the oracle's on-the-fly FP64 coupling
+    rows (Sec. 2.2), not only against the context path it shares kernels
+    with."""
+    from oracle import translation
+    sc = synth.random_cluster(31, 3, 120, 4, radius=100.0, fill=0.25, polydisperse=True)
+    x_np = synth.random_vector(31, 20, (sc.N, sc.nmax))
+    rows = [0, 1, 17, 58, 99, sc.N - 1]
+    ref = translation.coupling_matvec_rows(sc.positions, sc.k, sc.lmax, x_np, rows)
     pos4 = _positions4(sc)
-    # N * nmax * 16 bytes above 32 MiB: refused before any GPU work (the
-    # buffers are never touched)
-    code = B.celes_coupling_matvec_noalloc(50_000, 4, sc.k, pos4, x, y, precision=B.CELES_FP64, check=False)
+    for precision, dt, tol in [(B.CELES_FP64, torch.complex128, 1e-10), (B.CELES_FP32, torch.complex64, 1e-5)]:
+        x = torch.from_numpy(x_np).to(dt).cuda()
+        for _ in range(2):  # the second call reuses the scratch the first one wrote
+            y = torch.full_like(x, float("nan"))
+            B.celes_coupling_matvec_noalloc(sc.N, sc.lmax, sc.k, pos4, x, y, precision=precision)
+            torch.cuda.synchronize()
+            got = y.cpu().numpy().astype(np.complex128)[rows]
+            assert rel(got, ref) < tol
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    # N * nmax * 16 bytes above 32 MiB is refused before any GPU work.  The
+    # buffers are allocated at the full size anyway (about 38 MB each), so
+    # that a regression of the size check computes on valid memory and fails
+    # the assertion instead of touching memory out of bounds.
+    N, L = 50_000, 4
+    nmax = 2 * L * (L + 2)
+    g = np.arange(N)
+    p4 = np.zeros((N, 4))
+    p4[:, 0], p4[:, 1], p4[:, 2] = 400.0 * (g % 40), 400.0 * ((g // 40) % 40), 400.0 * (g // 1600)
+    pos4 = torch.from_numpy(p4).cuda()
+    x = torch.zeros((N, nmax), dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(x)
+    k = 2 * np.pi / 550.0
+    code = B.celes_coupling_matvec_noalloc(N, L, k, pos4, x, y, precision=B.CELES_FP64, check=False)
     assert code == B.CELES_ETOOBIG
-    code = B.celes_coupling_matvec_noalloc(sc.N, 4, sc.k, pos4, x, x, precision=B.CELES_FP64, check=False)
-    assert code == B.CELES_EINVAL
+    code = B.celes_coupling_matvec_noalloc(N, L, k, pos4, x, x, precision=B.CELES_FP64, check=False)
+    assert code in (B.CELES_ETOOBIG, B.CELES_EINVAL)
+    n_small = 1000
+    code = B.celes_coupling_matvec_noalloc(n_small, L, k, pos4, x, x, precision=B.CELES_FP64, check=False)
+    assert code == B.CELES_EINVAL  # x and y alias
