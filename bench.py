@@ -36,6 +36,7 @@ import subprocess
 import sys
 import threading
 import time
+from functools import partial
 
 import numpy as np
 
@@ -70,6 +71,14 @@ def parse():
                     help="skip the 1e-10 reference solve and the oracle residual on sampled rows")
     ap.add_argument("--plain-full", action="store_true",
                     help="also run the full-size plain FP64 GMRES solve to 1e-6 uncapped (about 10 min)")
+    ap.add_argument("--learned-c4", action="store_true",
+                    help="run only the learned-guess workload at its stated size (training and 100 evaluations)")
+    ap.add_argument("--c4-train", type=int, default=2000, help="--learned-c4: training ensembles")
+    ap.add_argument("--c4-eval", type=int, default=100, help="--learned-c4: evaluation ensembles (8000 spheres)")
+    ap.add_argument("--c4-epochs", type=int, default=20, help="--learned-c4: training epochs")
+    ap.add_argument("--c5", action="store_true",
+                    help="run only the 100 000-sphere workload end to end (preconditioned mixed solve to 1e-6)")
+    ap.add_argument("--c5-edge", type=float, default=1000.0, help="--c5: preconditioner cuboid edge (nm)")
     ap.add_argument("--case", choices=["coupling", "precond", "batch"], default=None,
                     help="run one operation on a synthetic case and print its time (profiling); see run_case")
     ap.add_argument("--lmax", type=int, default=4, help="--case: degree")
@@ -361,6 +370,173 @@ def run_learned(args, local_rank):
     finally:
         for c in train:
             B.celes_destroy(c)
+
+
+def _pack_config4(index, N=None):
+    """Worker: one learned-guess ensemble (positions, radii, n) by its seed."""
+    import synth
+    sc = synth.config4(index, N=N)
+    return index, sc.positions, sc.radii, sc.n_sphere, sc.name
+
+
+def run_learned_c4(args, local_rank):
+    """The learned initial guess at the stated learned-guess workload: the
+    graph network is trained on `--c4-train` solved ensembles (N ~ U[1000,
+    5000], lmax 3, fill ~ U[0.2, 0.4], R = 100 nm, n = 1.52, x-polarised plane
+    wave), then 100 unseen ensembles of 8000 spheres are solved from T a and
+    from the learned first iterate (mixed precision to 1e-6): GMRES
+    iterations, time (prediction included) and the final FP64 residual.
+    Packings are made by spawn workers on the host cores while the GPU solves.
+    Evaluation seeds (index 100 000 + e) are disjoint from training seeds."""
+    import multiprocessing as mp
+    import synth
+    from paper_1706_02145_gb300 import binding as B
+    cores = host_cores()
+    n_train, n_eval, epochs = args.c4_train, args.c4_eval, args.c4_epochs
+    out = {"train_ensembles": n_train, "eval_ensembles": n_eval, "epochs": epochs, "width": 128, "layers": 3,
+           "knn": 16, "eval_N": 8000}
+    g = B.celes_gnn_create(3, width=128, layers=3, seed=1, device=local_rank)
+    try:
+        t0 = time.perf_counter()
+        t_gpu = 0.0
+        train_its = []
+        with mp.get_context("spawn").Pool(max(1, cores - 1)) as pool:
+            for idx, pos, rad, nn, name in pool.imap_unordered(_pack_config4, range(n_train), chunksize=4):
+                tg = time.perf_counter()
+                c = B.celes_create(pos, rad, nn, 1.0, 2 * np.pi / 550.0, 3, device=local_rank)
+                try:
+                    B.celes_set_incident(c, [B.make_incident("plane", beta=0.0, alpha=0.0, pol=2)])
+                    info = B.celes_solve(c, 1e-7, mode=B.CELES_SOLVE_MIXED, raise_on_noconv=False)
+                    train_its.append(info["iterations"])
+                    B.celes_gnn_add_example(g, c)
+                finally:
+                    B.celes_destroy(c)
+                t_gpu += time.perf_counter() - tg
+            out["data_s"] = time.perf_counter() - t0
+            out["data_gpu_s"] = t_gpu
+            out["train_mean_iterations"] = float(np.mean(train_its))
+            # training: epochs over the stored examples in a seeded random order
+            rng = np.random.default_rng(3)
+            t0 = time.perf_counter()
+            losses = []
+            for ep in range(epochs):
+                lr = 1e-3 * (0.5 ** (ep // max(1, epochs // 4)))
+                ls = [B.celes_gnn_train_example(g, int(i), steps=1, lr=lr) for i in rng.permutation(n_train)]
+                losses.append(float(np.mean(ls)))
+            out["train_s"] = time.perf_counter() - t0
+            out["loss_per_epoch"] = losses
+            B.celes_gnn_clear_examples(g)
+            # evaluation on unseen 8000-sphere ensembles
+            rows = []
+            t0 = time.perf_counter()
+            for idx, pos, rad, nn, name in pool.imap(partial(_pack_config4, N=8000),
+                                                     [100_000 + e for e in range(n_eval)]):
+                c = B.celes_create(pos, rad, nn, 1.0, 2 * np.pi / 550.0, 3, device=local_rank)
+                try:
+                    B.celes_set_incident(c, [B.make_incident("plane", beta=0.0, alpha=0.0, pol=2)])
+                    base = B.celes_solve(c, TOL, mode=B.CELES_SOLVE_MIXED, raise_on_noconv=False)
+                    tp = time.perf_counter()
+                    B.celes_gnn_predict(g, c)
+                    t_pred = time.perf_counter() - tp
+                    lg = B.celes_solve(c, TOL, mode=B.CELES_SOLVE_MIXED, x0=B.CELES_X0_LEARNED,
+                                       raise_on_noconv=False)
+                    rows.append((base["iterations"], lg["iterations"], base["seconds"], lg["seconds"] + t_pred,
+                                 base["residual"], lg["residual"], lg["guess_used"], name))
+                finally:
+                    B.celes_destroy(c)
+            out["eval_s"] = time.perf_counter() - t0
+        its_b = np.array([r[0] for r in rows], float)
+        its_l = np.array([r[1] for r in rows], float)
+        out.update({"ta_mean_iterations": float(its_b.mean()), "learned_mean_iterations": float(its_l.mean()),
+                    "mean_iterations_saved": float((its_b - its_l).mean()),
+                    "ta_mean_s": float(np.mean([r[2] for r in rows])),
+                    "learned_mean_s": float(np.mean([r[3] for r in rows])),
+                    "max_final_residual": float(max(max(r[4], r[5]) for r in rows)),
+                    "guess_used_fraction": float(np.mean([r[6] for r in rows])),
+                    "per_ensemble": [{"ta_its": r[0], "learned_its": r[1], "name": r[7]} for r in rows[:20]]})
+        return out
+    finally:
+        B.celes_gnn_destroy(g)
+
+
+def run_c5(args, local_rank):
+    """The large workload end to end: 100 000 monodisperse spheres (R = 130
+    nm, n = 1.52, lmax 3) in a 4 um slab at fill 0.25, Gaussian beam of waist
+    5 um, the paper's block-diagonal preconditioner over 1 um cuboids
+    (Sec. 3.2.1), FP32 inner GMRES with FP64 refinement to 1e-6.  Reports the
+    packing, incident, preconditioner build and solve times, iterations, the
+    FP32 coupling matvec and preconditioner-apply times (CUDA events; the
+    apply as a fraction of the measured HBM bandwidth) and the oracle's
+    residual of the solution on sampled receiver rows (cpu_baseline leg)."""
+    import torch
+    import synth
+    from paper_1706_02145_gb300 import binding as B
+    out = {"workload": "100 000 spheres R=130nm n=1.52 lmax 3, 4um slab fill 0.25, Gaussian w=5um, "
+                       f"block-diagonal preconditioner {args.c5_edge:g} nm cuboids, mixed solve to 1e-6"}
+    t0 = time.perf_counter()
+    sc = synth.config5(0)
+    out["pack_s"] = time.perf_counter() - t0
+    inc_d = sc.incidents[0]
+    inc = B.make_incident("gaussian", waist=inc_d.waist, focus=inc_d.focus, alpha_G=inc_d.alpha_G, n_beta=128)
+    ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, device=local_rank)
+    try:
+        t0 = time.perf_counter()
+        B.celes_set_incident(ctx, [inc])
+        torch.cuda.synchronize()
+        out["incident_s"] = time.perf_counter() - t0
+
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            st = torch.cuda.current_stream()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn(sc.N, sc.nmax, dtype=torch.complex64, device="cuda", generator=g)
+        y = torch.empty_like(x)
+        st = torch.cuda.current_stream()
+        ms_mv = timed(lambda: B.celes_coupling_matvec(ctx, x, y, precision=B.CELES_FP32, stream=st), 3)
+        out["matvec_fp32_ms"] = ms_mv
+        out["matvec_fp32_couplings_per_s"] = sc.N * (sc.N - 1) / (ms_mv / 1e3)
+        t0 = time.perf_counter()
+        B.celes_precond_build(ctx, args.c5_edge)
+        out["precond_build_s"] = time.perf_counter() - t0
+        nb, maxd, ent = B.celes_precond_stats(ctx)
+        ms_ap = timed(lambda: B.celes_precond_apply(ctx, x, y, precision=B.CELES_FP32, stream=st), 5)
+        gbs = ent * 8 / (ms_ap / 1e3) / 1e9
+        hbm = None
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                hbm = json.load(fh).get("hbm_gbs")
+        except Exception:
+            pass
+        out["precond"] = {"blocks": nb, "max_block_dim": maxd, "factor_bytes_fp32": ent * 8,
+                          "factor_bytes_fp64": ent * 16, "apply_fp32_ms": ms_ap, "apply_gbs": gbs,
+                          "apply_frac_of_measured_hbm": (gbs / hbm) if hbm else None}
+        info = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_MIXED, use_precond=True, max_iter=20000,
+                             raise_on_noconv=False)
+        out["solve"] = {"s": info["seconds"], "iterations": info["iterations"], "outer": info["outer"],
+                        "matvecs_fp32": info["matvecs_fp32"], "matvecs_fp64": info["matvecs_fp64"],
+                        "residual_fp64_gpu": info["residual"], "status": info["status"]}
+        out["total_s"] = out["incident_s"] + out["precond_build_s"] + info["seconds"]
+        b = B.celes_get_coefficients(ctx)[0]
+    finally:
+        B.celes_destroy(ctx)
+    if not args.no_cpu:
+        import multiprocessing as mp
+        cores = host_cores()
+        rows = [int(r) for r in np.random.default_rng(11).choice(sc.N, 4 * cores, replace=False)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            (res,), rate, dt = certify_rows(sc, inc_d, [b], rows, cores, pool)
+        out["oracle_sampled_residual"] = {"rows": len(rows), "residual": res, "oracle_couplings_per_s": rate,
+                                          "oracle_s": dt, "cores": cores}
+    return out
 
 
 def max_over_ranks(x, dist, device):
@@ -776,8 +952,10 @@ def run_case(args):
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
     if args.case == "precond":
-        print(f"N={sc.N} lmax={sc.lmax} {args.precision} block preconditioner apply (edge {args.edge:g} nm): "
-              f"{t * 1e3:.3f} ms")
+        nb, maxd, ent = B.celes_precond_stats(ctx)
+        fb = ent * (8 if prec == B.CELES_FP32 else 16)
+        print(f"N={sc.N} lmax={sc.lmax} {args.precision} block preconditioner apply (edge {args.edge:g} nm, "
+              f"{nb} blocks, largest {maxd}): {t * 1e3:.3f} ms, factors {fb / 1e9:.3f} GB, {fb / t / 1e9:.1f} GB/s")
     else:
         pairs = sc.N * (sc.N - 1) * nrhs
         print(f"N={sc.N} lmax={sc.lmax} {args.precision} kernel={args.kernel} rhs={nrhs}: {t * 1e3:.3f} ms, "
@@ -792,6 +970,20 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.case:
         run_case(args)
+        return
+    if args.c5:
+        import torch
+        torch.cuda.set_device(local_rank)
+        from paper_1706_02145_gb300 import binding as B
+        B.load()
+        print(json.dumps({"large_c5": run_c5(args, local_rank)}), flush=True)
+        return
+    if args.learned_c4:
+        import torch
+        torch.cuda.set_device(local_rank)
+        from paper_1706_02145_gb300 import binding as B
+        B.load()
+        print(json.dumps({"learned_guess_c4": run_learned_c4(args, local_rank)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank)

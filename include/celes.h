@@ -162,6 +162,13 @@ int celes_master_matvec(celes_ctx* ctx, const void* x, void* y, int nrhs, int pr
  * the GPU.  Replaces any earlier preconditioner. */
 int celes_precond_build(celes_ctx* ctx, double cuboid_edge);
 
+/* Size of the built block preconditioner: number of blocks (cuboids that
+ * hold spheres), largest block dimension (unknowns) and the total number of
+ * complex entries of all blocks' factors (the apply reads each once: 16 bytes
+ * per entry for FP64 vectors, 8 for FP32).  CELES_ESTATE before a build.
+ * Measurement support; the paper has no counterpart. */
+int celes_precond_stats(const celes_ctx* ctx, int64_t* nblocks, int64_t* max_dim, int64_t* entries);
+
 /* y = P^{-1} x with P the block-diagonal part of M (Sec. 3.2.1, step 4):
  * per block, solve L_j U_j y = P_j x.  Layout as for the matvecs.  FP64
  * vectors use the FP64 factors; FP32 vectors an FP32 copy of them made at
@@ -296,6 +303,20 @@ typedef struct celes_gnn celes_gnn;
 int celes_gnn_create(celes_gnn** out, int lmax, int width, int layers, int knn, uint64_t seed, int device);
 int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps, double lr, double* loss_out);
 int celes_gnn_predict(celes_gnn* g, celes_ctx* ctx);
+/* Training over many ensembles without keeping their contexts:
+ *   celes_gnn_add_example  : copies a solved context's graph (16-NN lists),
+ *                            node and edge features and target (b - T a) of
+ *                            RHS `rhs` into the network's own device memory
+ *                            (about 1 KB per sphere) and returns its index in
+ *                            *idx; the context may then be destroyed;
+ *                            CELES_ESTATE if unsolved
+ *   celes_gnn_train_example: `steps` Adam steps on stored example idx
+ *                            (steps = 0: loss only); loss_out as in train
+ *   celes_gnn_num_examples / celes_gnn_clear_examples: count / free them. */
+int celes_gnn_add_example(celes_gnn* g, celes_ctx* ctx, int rhs, int* idx);
+int celes_gnn_train_example(celes_gnn* g, int idx, int steps, double lr, double* loss_out);
+int celes_gnn_num_examples(const celes_gnn* g);
+int celes_gnn_clear_examples(celes_gnn* g);
 int celes_gnn_num_params(const celes_gnn* g);
 /* Copy the parameters (what = 0) or the gradients of the last training pass
  * (what = 1) to `host` as FP32, layer by layer (input, then message and update

@@ -79,6 +79,8 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 # (name, restype, argtypes) of every exported symbol of include/celes.h
 SIGNATURES = [
+    ("celes_precond_stats", ctypes.c_int, [_c_ctx_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     ("celes_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("celes_create", ctypes.c_int, [ctypes.POINTER(_c_ctx_p), ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(celes_options)]),
@@ -115,6 +117,10 @@ SIGNATURES = [
                                         ctypes.c_int, ctypes.c_uint64, ctypes.c_int]),
     ("celes_gnn_train", ctypes.c_int, [ctypes.c_void_p, _c_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]),
     ("celes_gnn_predict", ctypes.c_int, [ctypes.c_void_p, _c_ctx_p]),
+    ("celes_gnn_add_example", ctypes.c_int, [ctypes.c_void_p, _c_ctx_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("celes_gnn_train_example", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]),
+    ("celes_gnn_num_examples", ctypes.c_int, [ctypes.c_void_p]),
+    ("celes_gnn_clear_examples", ctypes.c_int, [ctypes.c_void_p]),
     ("celes_gnn_num_params", ctypes.c_int, [ctypes.c_void_p]),
     ("celes_gnn_export", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.c_int]),
@@ -281,6 +287,13 @@ def celes_precond_apply(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
     _ctx_vec_checks(ctx, x, y, nrhs, precision)
     return _check(load().celes_precond_apply(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
                                              _stream(stream)), ctx)
+
+
+def celes_precond_stats(ctx):
+    """(blocks, largest block dimension, complex entries of all factors) of the built preconditioner."""
+    a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().celes_precond_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
+    return a.value, b.value, c.value
 
 
 def celes_set_initial_guess(ctx, b0):
@@ -451,6 +464,34 @@ def celes_gnn_train(g, ctx, rhs=0, steps=1, lr=1e-3):
     if code != CELES_OK:
         raise CelesError(code, "celes_gnn_train")
     return loss.value
+
+
+def celes_gnn_add_example(g, ctx, rhs=0):
+    """Store a solved context's training example in the network; returns its index."""
+    idx = ctypes.c_int(-1)
+    code = load().celes_gnn_add_example(g, ctx, int(rhs), ctypes.byref(idx))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_gnn_add_example")
+    return idx.value
+
+
+def celes_gnn_train_example(g, idx, steps=1, lr=1e-3):
+    """Adam steps on stored example idx; returns the last loss."""
+    loss = np.zeros(1)
+    code = load().celes_gnn_train_example(g, int(idx), int(steps), float(lr), _dptr(loss))
+    if code != CELES_OK:
+        raise CelesError(code, "celes_gnn_train_example")
+    return float(loss[0])
+
+
+def celes_gnn_num_examples(g):
+    return int(load().celes_gnn_num_examples(g))
+
+
+def celes_gnn_clear_examples(g):
+    code = load().celes_gnn_clear_examples(g)
+    if code != CELES_OK:
+        raise CelesError(code, "celes_gnn_clear_examples")
 
 
 def celes_gnn_predict(g, ctx):

@@ -167,6 +167,7 @@ struct celes_ctx {
   // preconditioner
   bool has_precond = false;
   int64_t nblocks = 0;
+  int64_t mat_entries = 0;  // complex entries of all blocks' factors
   int max_block_dim = 0;
   DevBuf block_off, mat_off, perm, mats, mats32, piv, pivperm, info, pwork;
   // small device scratch
@@ -674,8 +675,18 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
   for (int64_t q = 0; q < nb; ++q)
     if (hinfo[q] != 0) return fail(c, CELES_ENUMERIC, "precond_build: block %lld is singular", (long long)q);
   c->nblocks = nb;
+  c->mat_entries = moff[nb];
   c->max_block_dim = static_cast<int>(max_dim);
   c->has_precond = true;
+  return CELES_OK;
+}
+
+extern "C" int celes_precond_stats(const celes_ctx* c, int64_t* nblocks, int64_t* max_dim, int64_t* entries) {
+  if (!c) return CELES_EINVAL;
+  if (!c->has_precond) return CELES_ESTATE;
+  if (nblocks) *nblocks = c->nblocks;
+  if (max_dim) *max_dim = c->max_block_dim;
+  if (entries) *entries = c->mat_entries;
   return CELES_OK;
 }
 

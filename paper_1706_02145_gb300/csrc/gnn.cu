@@ -365,6 +365,14 @@ struct celes_gnn {
   std::vector<std::unique_ptr<Buf>> h, xe, zm, mm, agg, u, zu, yu;
   Buf o, dout, dh, dh2, dzu, du, dm, dxe, t1, t2, t3, lossd, err, tmp16;
   std::string errmsg;
+  // stored training examples (celes_gnn_add_example): each keeps its graph,
+  // features and target in device memory, so that training passes over many
+  // ensembles need no neighbour search and no context
+  struct Example {
+    int64_t N = 0;
+    Buf nbr, rev_off, rev_edge, ef, feat, tgt;
+  };
+  std::vector<std::unique_ptr<Example>> examples;
 };
 
 namespace {
@@ -730,6 +738,128 @@ extern "C" void celes_gnn_destroy(celes_gnn* g) {
   cudaSetDevice(prev);
 }
 
+namespace {
+
+// `steps` Adam steps (0: loss and gradients only) on the graph, features and
+// target currently in the working buffers
+int train_steps(celes_gnn* g, int64_t N, int steps, double lr, double* loss_out) {
+  int s = CELES_OK;
+  double loss = 0.0;
+  const int passes = steps > 0 ? steps : 1;
+  for (int it = 0; it < passes && !s; ++it) {
+    s = forward(g, N);
+    if (s) break;
+    if (cudaMemsetAsync(g->lossd.p, 0, 8, g->stream) != cudaSuccess) {
+      s = CELES_ECUDA;
+      break;
+    }
+    mse_kernel<<<256, 256, 0, g->stream>>>(N * g->OUTP, g->o.as<float>(), g->tgt.as<float>(), g->dout.as<float>(),
+                                           g->lossd.as<double>());
+    note_launch();
+    s = backward(g, N);
+    if (!s && steps > 0) s = adam(g, static_cast<float>(lr));
+    if (!s && it == passes - 1 &&
+        cudaMemcpyAsync(&loss, g->lossd.p, 8, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+      s = CELES_ECUDA;
+  }
+  if (!s) s = check_err(g);
+  if (!s && loss_out) *loss_out = loss;
+  return s;
+}
+
+// the target (b - T a) * scale of RHS `rhs`, padded to OUTP columns, into g->tgt
+int make_target(celes_gnn* g, const CtxView& v, int rhs, double scale) {
+  const int64_t N = v.N;
+  const int64_t n = N * v.nmax * 2;
+  Buf tmp;
+  if (tmp.ensure(n * 4) != cudaSuccess) return CELES_ENOMEM;
+  target_kernel<<<blocks(n), 256, 0, g->stream>>>(n, v.b + (size_t)rhs * n, v.rhs + (size_t)rhs * n, scale,
+                                                   tmp.as<float>());
+  note_launch();
+  GK(cudaMemsetAsync(g->tgt.p, 0, N * g->OUTP * 4, g->stream));
+  GK(cudaMemcpy2DAsync(g->tgt.p, g->OUTP * 4, tmp.p, v.nmax * 2 * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
+                       g->stream));
+  GK(cudaStreamSynchronize(g->stream));  // tmp is released on return
+  return CELES_OK;
+}
+
+}  // namespace
+
+extern "C" int celes_gnn_add_example(celes_gnn* g, celes_ctx* ctx, int rhs, int* idx) {
+  celes::NvtxRange nvtx_range_("celes_gnn_add_example");
+  if (!g || !ctx) return CELES_EINVAL;
+  CtxView v{};
+  int s = ctx_view(ctx, &v);
+  if (s) return s;
+  if (v.L != g->lmax || rhs < 0 || rhs >= v.nrhs) return CELES_EINVAL;
+  if (!v.has_b) return CELES_ESTATE;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  double scale = 1.0;
+  s = prepare(g, v, rhs, scale);
+  if (!s) s = make_target(g, v, rhs, scale);
+  if (!s) {
+    std::unique_ptr<celes_gnn::Example> ex(new celes_gnn::Example());
+    const int64_t N = v.N, E = N * g->knn;
+    ex->N = N;
+    struct Cp {
+      Buf* dst;
+      const Buf* src;
+      size_t bytes;
+    } cps[] = {{&ex->nbr, &g->nbr, (size_t)E * 4},        {&ex->rev_off, &g->rev_off, (size_t)(N + 1) * 4},
+               {&ex->rev_edge, &g->rev_edge, (size_t)E * 4}, {&ex->ef, &g->ef, (size_t)E * kEdgeFeat * 4},
+               {&ex->feat, &g->feat, (size_t)N * g->F * 2}, {&ex->tgt, &g->tgt, (size_t)N * g->OUTP * 4}};
+    for (auto& c : cps) {
+      if (s) break;
+      if (c.dst->ensure(c.bytes) != cudaSuccess) s = CELES_ENOMEM;
+      else if (cudaMemcpyAsync(c.dst->p, c.src->p, c.bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
+        s = CELES_ECUDA;
+    }
+    if (!s && cudaStreamSynchronize(g->stream) != cudaSuccess) s = CELES_ECUDA;
+    if (!s) {
+      g->examples.push_back(std::move(ex));
+      if (idx) *idx = static_cast<int>(g->examples.size()) - 1;
+    }
+  }
+  cudaSetDevice(prev);
+  return s;
+}
+
+extern "C" int celes_gnn_num_examples(const celes_gnn* g) { return g ? static_cast<int>(g->examples.size()) : 0; }
+
+extern "C" int celes_gnn_clear_examples(celes_gnn* g) {
+  if (!g) return CELES_EINVAL;
+  g->examples.clear();
+  return CELES_OK;
+}
+
+extern "C" int celes_gnn_train_example(celes_gnn* g, int idx, int steps, double lr, double* loss_out) {
+  celes::NvtxRange nvtx_range_("celes_gnn_train_example");
+  if (!g || idx < 0 || idx >= static_cast<int>(g->examples.size()) || steps < 0 || !(lr > 0.0)) return CELES_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  const celes_gnn::Example& ex = *g->examples[idx];
+  const int64_t N = ex.N, E = N * g->knn;
+  int s = ensure_capacity(g, N);
+  struct Cp {
+    Buf* dst;
+    const Buf* src;
+    size_t bytes;
+  } cps[] = {{&g->nbr, &ex.nbr, (size_t)E * 4},        {&g->rev_off, &ex.rev_off, (size_t)(N + 1) * 4},
+             {&g->rev_edge, &ex.rev_edge, (size_t)E * 4}, {&g->ef, &ex.ef, (size_t)E * kEdgeFeat * 4},
+             {&g->feat, &ex.feat, (size_t)N * g->F * 2}, {&g->tgt, &ex.tgt, (size_t)N * g->OUTP * 4}};
+  for (auto& c : cps) {
+    if (s) break;
+    if (cudaMemcpyAsync(c.dst->p, c.src->p, c.bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
+      s = CELES_ECUDA;
+  }
+  if (!s) s = train_steps(g, N, steps, lr, loss_out);
+  cudaSetDevice(prev);
+  return s;
+}
+
 extern "C" int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps, double lr, double* loss_out) {
   celes::NvtxRange nvtx_range_("celes_gnn_train");
   if (!g || !ctx || steps < 0 || !(lr > 0.0)) return CELES_EINVAL;
@@ -743,43 +873,8 @@ extern "C" int celes_gnn_train(celes_gnn* g, celes_ctx* ctx, int rhs, int steps,
   cudaSetDevice(g->device);
   double scale = 1.0;
   s = prepare(g, v, rhs, scale);
-  const int64_t N = v.N;
-  if (!s) {
-    const int64_t n = N * v.nmax * 2;
-    // target (b - T a) * scale, padded to OUTP columns
-    Buf tmp;
-    if (tmp.ensure(n * 4) != cudaSuccess) s = CELES_ENOMEM;
-    if (!s) {
-      target_kernel<<<blocks(n), 256, 0, g->stream>>>(n, v.b + (size_t)rhs * n, v.rhs + (size_t)rhs * n, scale,
-                                                       tmp.as<float>());
-      note_launch();
-      if (cudaMemsetAsync(g->tgt.p, 0, N * g->OUTP * 4, g->stream) != cudaSuccess ||
-          cudaMemcpy2DAsync(g->tgt.p, g->OUTP * 4, tmp.p, v.nmax * 2 * 4, v.nmax * 2 * 4, N, cudaMemcpyDeviceToDevice,
-                            g->stream) != cudaSuccess)
-        s = CELES_ECUDA;
-      double loss = 0.0;
-      // steps = 0: loss and gradients only (no update)
-      const int passes = steps > 0 ? steps : 1;
-      for (int it = 0; it < passes && !s; ++it) {
-        s = forward(g, N);
-        if (s) break;
-        if (cudaMemsetAsync(g->lossd.p, 0, 8, g->stream) != cudaSuccess) {
-          s = CELES_ECUDA;
-          break;
-        }
-        mse_kernel<<<256, 256, 0, g->stream>>>(N * g->OUTP, g->o.as<float>(), g->tgt.as<float>(),
-                                               g->dout.as<float>(), g->lossd.as<double>());
-        note_launch();
-        s = backward(g, N);
-        if (!s && steps > 0) s = adam(g, static_cast<float>(lr));
-        if (!s && it == passes - 1 &&
-            cudaMemcpyAsync(&loss, g->lossd.p, 8, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
-          s = CELES_ECUDA;
-      }
-      if (!s) s = check_err(g);
-      if (!s && loss_out) *loss_out = loss;
-    }
-  }
+  if (!s) s = make_target(g, v, rhs, scale);
+  if (!s) s = train_steps(g, v.N, steps, lr, loss_out);
   cudaSetDevice(prev);
   return s;
 }

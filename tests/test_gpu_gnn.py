@@ -152,3 +152,59 @@ def test_gnn_training_and_learned_guess_solve():
         B.celes_gnn_destroy(g)
         for _, ctx in train:
             B.celes_destroy(ctx)
+
+
+def test_gnn_at_the_learned_guess_shape_matches_autograd():
+    # width 128, 3 message-passing layers, lmax 3 (the stated network)
+    L, W, layers = 3, 128, 3
+    sc, ctx = _solved(7, 150, L)
+    g = B.celes_gnn_create(L, width=W, layers=layers, seed=11)
+    try:
+        B.celes_gnn_train(g, ctx, steps=1, lr=1e-2)
+        params = B.celes_gnn_export(g, 0)
+        loss = B.celes_gnn_train(g, ctx, steps=0)
+        grads = B.celes_gnn_export(g, 1)
+        ref_loss, ref_grads, shapes = _reference(sc, ctx, params, W, layers, L)
+        assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss)
+        off = 0
+        for (o, i) in shapes:
+            n = o * i + o
+            a, r = grads[off:off + n], ref_grads[off:off + n]
+            assert np.linalg.norm(a - r) <= 3e-2 * np.linalg.norm(r) + 1e-12, (o, i)
+            off += n
+    finally:
+        B.celes_gnn_destroy(g)
+        B.celes_destroy(ctx)
+
+
+def test_gnn_stored_examples_train_like_their_contexts():
+    # an example stored from a context and then trained without it gives the
+    # same losses and parameters as training on the context itself
+    L = 2
+    sc, ctx = _solved(3, 120, L)
+    g1 = B.celes_gnn_create(L, width=32, layers=2, seed=9)
+    g2 = B.celes_gnn_create(L, width=32, layers=2, seed=9)
+    try:
+        idx = B.celes_gnn_add_example(g2, ctx)
+        assert idx == 0 and B.celes_gnn_num_examples(g2) == 1
+        B.celes_destroy(ctx)
+        ctx = None
+        sc2, ctx2 = _solved(3, 120, L)
+        try:
+            l1 = [B.celes_gnn_train(g1, ctx2, steps=1, lr=3e-3) for _ in range(5)]
+        finally:
+            B.celes_destroy(ctx2)
+        l2 = [B.celes_gnn_train_example(g2, idx, steps=1, lr=3e-3) for _ in range(5)]
+        assert np.allclose(l1, l2, rtol=1e-5, atol=0)
+        # (the feature scale is a sum reduced with atomics: equal to rounding)
+        p1, p2 = B.celes_gnn_export(g1, 0), B.celes_gnn_export(g2, 0)
+        assert np.linalg.norm(p1 - p2) <= 1e-5 * np.linalg.norm(p1)
+        B.celes_gnn_clear_examples(g2)
+        assert B.celes_gnn_num_examples(g2) == 0
+        with pytest.raises(B.CelesError):
+            B.celes_gnn_train_example(g2, 0)
+    finally:
+        B.celes_gnn_destroy(g1)
+        B.celes_gnn_destroy(g2)
+        if ctx is not None:
+            B.celes_destroy(ctx)

@@ -86,6 +86,38 @@ def test_config3_grows_the_cube_when_the_drawn_fill_cannot_be_packed():
     assert np.array_equal(sc.positions, again.positions)
 
 
+@pytest.mark.parametrize("fill", [0.25, 0.38, 0.4])
+def test_config4_cube_at_its_drawn_fill(fill):
+    # fills above 0.3 come from an FCC lattice shaken by hard-sphere Monte
+    # Carlo; every ensemble holds exactly its fill, inside the walls, disjoint
+    sc = synth.config4(5, N=1200, fill=fill, sweeps=40)
+    assert sc.N == 1200 and sc.lmax == 3 and np.all(sc.radii == 100.0) and np.all(sc.n_sphere == 1.52)
+    side = (_volume(sc) / fill) ** (1.0 / 3.0)
+    assert np.all(sc.positions >= 100.0 - 1e-9) and np.all(sc.positions <= side - 100.0 + 1e-9)
+    assert _disjoint(sc)
+    assert sc.incidents[0].kind == "plane" and sc.incidents[0].pol == 2
+
+
+def test_config4_shake_moves_the_lattice():
+    # the Monte-Carlo sweeps displace the spheres from their lattice sites
+    rng = synth.rng_for(4, 99)
+    side = (1000 * 4.0 / 3.0 * np.pi * 100.0 ** 3 / 0.38) ** (1.0 / 3.0)
+    p0 = synth.fcc_shaken_cube(synth.rng_for(4, 99), 1000, 100.0, side, sweeps=0)
+    p1 = synth.fcc_shaken_cube(rng, 1000, 100.0, side, sweeps=30)
+    moved = np.linalg.norm(p1 - p0, axis=1)
+    assert np.median(moved) > 5.0
+
+
+def test_config4_fill_draws_span_the_recipe():
+    def draw(i):
+        rng = synth.rng_for(4, i)
+        return int(rng.integers(1000, 5001)), float(rng.uniform(0.2, 0.4))
+    sizes, fills = zip(*[draw(i) for i in range(200)])
+    assert min(fills) < 0.22 and max(fills) > 0.38
+    assert min(sizes) < 1200 and max(sizes) > 4800
+    assert synth.config4(7, N=1000, sweeps=5).name.endswith(f"fill={draw(7)[1]:.3f}")
+
+
 def test_config5_slab_at_reduced_size():
     sc = synth.config5(0, N=4000)
     assert sc.lmax == 3 and np.all(sc.radii == 130.0)
