@@ -485,10 +485,13 @@ def run_c5(args, local_rank):
         torch.cuda.synchronize()
         out["incident_s"] = time.perf_counter() - t0
 
+        # a stream of its own: the binding passes NULL for the legacy default
+        # stream, which would launch on the context's stream instead
+        st = torch.cuda.Stream()
+
         def timed(fn, reps):
             fn()
             torch.cuda.synchronize()
-            st = torch.cuda.current_stream()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
             for _ in range(reps):
@@ -500,7 +503,6 @@ def run_c5(args, local_rank):
         g = torch.Generator(device="cuda").manual_seed(0)
         x = torch.randn(sc.N, sc.nmax, dtype=torch.complex64, device="cuda", generator=g)
         y = torch.empty_like(x)
-        st = torch.cuda.current_stream()
         ms_mv = timed(lambda: B.celes_coupling_matvec(ctx, x, y, precision=B.CELES_FP32, stream=st), 3)
         out["matvec_fp32_ms"] = ms_mv
         out["matvec_fp32_couplings_per_s"] = sc.N * (sc.N - 1) / (ms_mv / 1e3)

@@ -170,6 +170,8 @@ struct celes_ctx {
   int64_t mat_entries = 0;  // complex entries of all blocks' factors
   int max_block_dim = 0;
   DevBuf block_off, mat_off, perm, mats, mats32, piv, pivperm, info, pwork;
+  DevBuf tile_off, tinv, tinv32;  // explicit inverses of the diagonal 32 x 32 tiles of L and U
+  int precond_csize = 1;          // CTAs per block in the cluster-form apply
   // small device scratch
   DevBuf dots, dot_partial, flag;
   std::string err;
@@ -455,6 +457,9 @@ extern "C" void celes_destroy(celes_ctx* c) {
     c->mats.release();
     c->mats32.release();
     c->pivperm.release();
+    c->tile_off.release();
+    c->tinv.release();
+    c->tinv32.release();
     c->piv.release();
     c->info.release();
     c->pwork.release();
@@ -639,14 +644,17 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
   }
   boff.push_back(c->N);
   const int64_t nb = static_cast<int64_t>(boff.size()) - 1;
-  std::vector<int64_t> moff(nb + 1, 0);
-  int64_t max_pairs = 0, max_dim = 0;
+  std::vector<int64_t> moff(nb + 1, 0), toff(nb + 1, 0);
+  int64_t max_pairs = 0, max_dim = 0, max_tiles = 0;
   for (int64_t q = 0; q < nb; ++q) {
     const int64_t ns = boff[q + 1] - boff[q];
     const int64_t n = ns * c->nmax;
+    const int64_t nt = (n + 31) / 32;
     moff[q + 1] = moff[q] + n * n;
+    toff[q + 1] = toff[q] + nt * 2048;
     max_pairs = std::max(max_pairs, ns * ns);
     max_dim = std::max(max_dim, n);
+    max_tiles = std::max(max_tiles, nt);
   }
   c->has_precond = false;
   CK(c->block_off.ensure(sizeof(int64_t) * (nb + 1)), "block offsets");
@@ -666,6 +674,17 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
                        c->piv.as<int>(), c->info.as<int>(), c->stream),
      "precond LU");
   CK(launch_f64_to_f32(2 * moff[nb], c->mats.as<double>(), c->mats32.as<float>(), c->stream), "FP32 factors");
+  CK(c->tile_off.ensure(sizeof(int64_t) * (nb + 1)), "tile offsets");
+  CK(c->tinv.ensure(sizeof(double) * 2 * toff[nb]), "tile inverses");
+  CK(c->tinv32.ensure(sizeof(float) * 2 * toff[nb]), "tile inverses (FP32 copy)");
+  CK(cudaMemcpyAsync(c->tile_off.p, toff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, c->stream),
+     "h2d");
+  CK(launch_precond_tile_inverse(nb, max_tiles, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(),
+                                 c->tile_off.as<int64_t>(), c->nmax, c->mats.as<double>(), c->tinv.as<double>(),
+                                 c->stream),
+     "tile inverses");
+  CK(launch_f64_to_f32(2 * toff[nb], c->tinv.as<double>(), c->tinv32.as<float>(), c->stream), "FP32 tile inverses");
+  c->precond_csize = precond_cluster_size(static_cast<double>(toff[nb] / 2048) / static_cast<double>(nb));
   CK(c->pivperm.ensure(sizeof(int) * c->N * c->nmax), "pivot permutation");
   CK(launch_pivot_perm(nb, c->block_off.as<int64_t>(), c->nmax, c->piv.as<int>(), c->pivperm.as<int>(), c->stream),
      "pivot permutation");
@@ -695,12 +714,16 @@ static int precond_apply_internal(celes_ctx* c, const void* x, void* y, int nrhs
   if (precision == CELES_FP64)
     CK(launch_precond_apply<double>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
                                     c->perm.as<int>(), c->mats.as<double>(), c->mats32.as<float>(), c->pivperm.as<int>(),
-                                    c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st),
+                                    c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st,
+                                    c->tile_off.as<int64_t>(), c->tinv.as<double>(), c->tinv32.as<float>(),
+                                    c->precond_csize),
        "precond apply");
   else
     CK(launch_precond_apply<float>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
                                    c->perm.as<int>(), c->mats.as<double>(), c->mats32.as<float>(), c->pivperm.as<int>(),
-                                   c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st),
+                                   c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st,
+                                   c->tile_off.as<int64_t>(), c->tinv.as<double>(), c->tinv32.as<float>(),
+                                   c->precond_csize),
        "precond apply");
   return CELES_OK;
 }

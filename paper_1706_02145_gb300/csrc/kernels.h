@@ -116,10 +116,19 @@ cudaError_t launch_precond_assemble(int L, int64_t nblocks, const int64_t* block
                                     int64_t max_pairs, cudaStream_t st);
 cudaError_t launch_precond_lu(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
                               double* mats, int* piv, int* info, cudaStream_t st);
+// tile_off/tinv/tinv32: explicit inverses of the 32 x 32 diagonal tiles of
+// each block's L and U (launch_precond_tile_inverse; tinv = nullptr selects
+// the one-CTA-per-block substitution); csize: CTAs per block (cluster size)
 template <typename R>
 cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
                                  const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
-                                 int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st);
+                                 int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st,
+                                 const int64_t* tile_off = nullptr, const double* tinv = nullptr,
+                                 const float* tinv32 = nullptr, int csize = 0);
+cudaError_t launch_precond_tile_inverse(int64_t nblocks, int64_t max_tiles, const int64_t* block_off,
+                                        const int64_t* mat_off, const int64_t* tile_off, int nmax, const double* mats,
+                                        double* tinv, cudaStream_t st);
+int precond_cluster_size(double mean_tiles);
 // per block, the gather permutation equivalent to the LU's row interchanges
 cudaError_t launch_pivot_perm(int64_t nblocks, const int64_t* block_off, int nmax, const int* piv, int* pivperm,
                               cudaStream_t st);

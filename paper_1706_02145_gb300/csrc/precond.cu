@@ -7,6 +7,7 @@
 // factors overwrite it in place (unit lower L below the diagonal, U on and
 // above), piv holds the LAPACK-style row interchanges (row k swapped with
 // piv[k] at step k).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -246,6 +247,174 @@ __global__ void __launch_bounds__(256) precond_apply_kernel(const int64_t* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// apply, cluster form: each block's triangular solves are spread over a
+// thread-block cluster of C CTAs (distributed shared memory).  CTA s of the
+// cluster owns a contiguous run of the block's 32-row tiles.  Per tile step
+// the owner multiplies its (updated) tile by the explicit inverse of the
+// 32 x 32 diagonal tile of L (forward) or U (backward), both formed at build
+// time, and writes the 32 solved values into every CTA's copy of the block
+// vector; after one cluster barrier every CTA applies that tile column to its
+// own rows.  The serial chain of a block is then one barrier and one short
+// GEMV per tile, the factor traffic is spread over C SMs, and blocks much
+// fewer than SMs still fill the GPU.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+// explicit inverses of the diagonal tiles of each block's LU (unit lower L,
+// upper U), column-major 32 x 32 each, tiles beyond the block padded with the
+// identity; one CTA of 64 threads per tile (32 columns of Linv, 32 of Uinv)
+__global__ void __launch_bounds__(64) precond_tile_inverse_kernel(const int64_t* __restrict__ block_off,
+                                                                  const int64_t* __restrict__ mat_off,
+                                                                  const int64_t* __restrict__ tile_off, int nmax,
+                                                                  const double2* __restrict__ mats,
+                                                                  double2* __restrict__ tinv) {
+  const int64_t q = blockIdx.y;
+  const int64_t n = (block_off[q + 1] - block_off[q]) * nmax;
+  const int64_t ntile = (n + 31) / 32;
+  const int64_t k = blockIdx.x;
+  if (k >= ntile) return;
+  const int64_t kb = k * 32;
+  const int tb = static_cast<int>(n - kb < 32 ? n - kb : 32);
+  const double2* A = mats + mat_off[q];
+  __shared__ double2 t[32][33];  // t[c][r] = A[kb + r, kb + c]
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int c = e >> 5, r = e & 31;
+    t[c][r] = (r < tb && c < tb) ? A[(kb + r) + (kb + c) * n] : make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  double2* Li = tinv + tile_off[q] + k * 2048;
+  double2* Ui = Li + 1024;
+  const int j = threadIdx.x & 31;
+  cd x[32];
+  if (threadIdx.x < 32) {
+    // column j of L^{-1}: L x = e_j, unit diagonal
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      cd acc = mkc(r == j ? 1.0 : 0.0);
+#pragma unroll
+      for (int c = 0; c < r; ++c) {
+        if (r < tb && c < tb) acc = acc - mkc(t[c][r].x, t[c][r].y) * x[c];
+      }
+      x[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) Li[j * 32 + r] = make_double2(x[r].re, x[r].im);
+  } else {
+    // column j of U^{-1}: U x = e_j
+#pragma unroll
+    for (int r = 31; r >= 0; --r) {
+      cd acc = mkc(r == j ? 1.0 : 0.0);
+#pragma unroll
+      for (int c = r + 1; c < 32; ++c) acc = acc - mkc(t[c][r].x, t[c][r].y) * x[c];
+      x[r] = acc / mkc(t[r][r].x, t[r][r].y);
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) Ui[j * 32 + r] = make_double2(x[r].re, x[r].im);
+  }
+}
+
+cudaError_t launch_precond_tile_inverse(int64_t nblocks, int64_t max_tiles, const int64_t* block_off,
+                                        const int64_t* mat_off, const int64_t* tile_off, int nmax, const double* mats,
+                                        double* tinv, cudaStream_t st) {
+  if (nblocks <= 0 || max_tiles <= 0) return cudaSuccess;
+  dim3 grid(static_cast<unsigned>(max_tiles), static_cast<unsigned>(nblocks));
+  precond_tile_inverse_kernel<<<grid, 64, 0, st>>>(block_off, mat_off, tile_off, nmax,
+                                                   reinterpret_cast<const double2*>(mats),
+                                                   reinterpret_cast<double2*>(tinv));
+  note_launch();
+  return cudaGetLastError();
+}
+
+constexpr int kApplyThreads = 256;
+constexpr int kApplyClusterMaxSmem = 160 * 1024;  // largest block vector of the cluster form
+
+// the CTA of cluster rank s owns tiles [s * per, min(ntile, (s + 1) * per))
+template <typename R, typename F>
+__global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
+    const int64_t* __restrict__ block_off, const int64_t* __restrict__ mat_off, const int64_t* __restrict__ tile_off,
+    int nmax, const int* __restrict__ perm, const Pair2<F>* __restrict__ mats, const Pair2<F>* __restrict__ tinv,
+    const int* __restrict__ pivperm, int64_t N, const Pair2<R>* __restrict__ x, Pair2<R>* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char pc_smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = static_cast<int>(cluster.num_blocks());
+  const int s = static_cast<int>(cluster.block_rank());
+  const int64_t q = blockIdx.x / C;
+  const int rhs = blockIdx.y;
+  const int64_t s0 = block_off[q];
+  const int64_t n = (block_off[q + 1] - s0) * nmax;
+  const int64_t ntile = (n + 31) / 32;
+  const int64_t per = (ntile + C - 1) / C;
+  const int64_t t_lo = s * per < ntile ? s * per : ntile;
+  const int64_t t_hi = (s + 1) * per < ntile ? (s + 1) * per : ntile;
+  const int64_t r_lo = t_lo * 32, r_hi = t_hi * 32 < n ? t_hi * 32 : n;
+  const Pair2<F>* A = mats + mat_off[q];
+  const Pair2<F>* TI = tinv + tile_off[q];
+  const int* pp = pivperm + s0 * nmax;
+  const Pair2<R>* xr = x + (int64_t)rhs * N * nmax;
+  Pair2<R>* yr = y + (int64_t)rhs * N * nmax;
+  Pair2<F>* v = reinterpret_cast<Pair2<F>*>(pc_smem);  // [n]: own rows (partial sums) + solved tiles
+  __shared__ Pair2<F> dt[32][33];
+  __shared__ Pair2<F> w[32];
+  // gather own rows (the pivot permutation folded in)
+  for (int64_t t = r_lo + threadIdx.x; t < r_hi; t += blockDim.x) {
+    const int64_t src = pp[t];
+    const int64_t a = src / nmax;
+    const int r = static_cast<int>(src - a * nmax);
+    const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
+    v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  // one triangular sweep; fwd: tiles 0..ntile-1 with L, else ntile-1..0 with U
+  auto sweep = [&](bool fwd) {
+    for (int64_t step = 0; step < ntile; ++step) {
+      const int64_t k = fwd ? step : ntile - 1 - step;
+      const int64_t kb = k * 32;
+      const int tb = static_cast<int>(n - kb < 32 ? n - kb : 32);
+      const bool owner = k >= t_lo && k < t_hi;
+      if (owner) {
+        const Pair2<F>* Ti = TI + k * 2048 + (fwd ? 0 : 1024);
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          F re = 0, im = 0;
+#pragma unroll 8
+          for (int c = 0; c < 32; ++c) {
+            if (c < tb) {
+              const Pair2<F> a = dt[c][lane], u = v[kb + c];
+              re += a.re * u.re - a.im * u.im;
+              im += a.re * u.im + a.im * u.re;
+            }
+          }
+          w[lane] = Pair2<F>{re, im};
+        }
+        __syncthreads();
+        // the solved tile into every CTA's copy of the block vector
+        for (int e = threadIdx.x; e < C * 32; e += blockDim.x) {
+          const int dst = e >> 5, r = e & 31;
+          if (r < tb) cluster.map_shared_rank(v, dst)[kb + r] = w[r];
+        }
+      }
+      cluster.sync();
+      // apply tile column k to own rows below (fwd) / above (back) the tile
+      const int64_t a0 = fwd ? (r_lo > kb + tb ? r_lo : kb + tb) : r_lo;
+      const int64_t a1 = fwd ? r_hi : (r_hi < kb ? r_hi : kb);
+      for (int64_t i = a0 + threadIdx.x; i < a1; i += blockDim.x) v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+      __syncthreads();
+    }
+  };
+  sweep(true);
+  sweep(false);
+  for (int64_t t = r_lo + threadIdx.x; t < r_hi; t += blockDim.x) {
+    const int64_t a = t / nmax;
+    const int r = static_cast<int>(t - a * nmax);
+    yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
+  }
+  // no CTA leaves while others may still write its shared memory
+  cluster.sync();
+}
+
 // position -> source index of the row interchanges of each block's LU
 // (applied in order kk = 0..n-1, as the factorisation recorded them)
 __global__ void pivot_perm_kernel(const int64_t* __restrict__ block_off, int nmax, const int* __restrict__ piv,
@@ -305,12 +474,64 @@ cudaError_t launch_apply_t(int64_t nblocks, const int64_t* block_off, const int6
   return cudaGetLastError();
 }
 
-// FP64 vectors use the FP64 factors; FP32 vectors the FP32 copy (mats32)
+template <typename R, typename F>
+cudaError_t launch_apply_cluster_t(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off,
+                                   const int64_t* tile_off, int nmax, const int* perm, const void* mats,
+                                   const void* tinv, const int* pivperm, int64_t N, int nrhs, const void* x, void* y,
+                                   int max_block_dim, int csize, cudaStream_t st) {
+  const size_t smem = sizeof(Pair2<F>) * static_cast<size_t>(max_block_dim);
+  static PerDevice attr;
+  cudaError_t se = cudaSuccess;
+  if (attr.get(current_device, [&] {
+        se = cudaFuncSetAttribute(precond_apply_cluster_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kApplyClusterMaxSmem);
+        return se == cudaSuccess ? 1 : 0;
+      }) == 0)
+    return se != cudaSuccess ? se : cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(nblocks * csize), static_cast<unsigned>(nrhs));
+  cfg.blockDim = dim3(kApplyThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(csize);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, precond_apply_cluster_kernel<R, F>, block_off, mat_off, tile_off, nmax,
+                                           perm, static_cast<const Pair2<F>*>(mats), static_cast<const Pair2<F>*>(tinv),
+                                           pivperm, N, static_cast<const Pair2<R>*>(x), static_cast<Pair2<R>*>(y));
+  note_launch();
+  return e;
+}
+
+// cluster size of the apply for blocks of about `mean_tiles` 32-row tiles
+int precond_cluster_size(double mean_tiles) {
+  if (mean_tiles >= 12.0) return 4;
+  if (mean_tiles >= 4.0) return 2;
+  return 1;
+}
+
+// FP64 vectors use the FP64 factors; FP32 vectors the FP32 copy (mats32).
+// With tile inverses (tinv non-null) and a block vector that fits in shared
+// memory, the cluster form runs; otherwise the one-CTA-per-block form.
 template <typename R>
 cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
                                  const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
-                                 int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st) {
+                                 int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st,
+                                 const int64_t* tile_off, const double* tinv, const float* tinv32, int csize) {
   if (nblocks <= 0) return cudaSuccess;
+  constexpr size_t esz = sizeof(R) == 8 ? 16 : 8;
+  if (tinv && csize >= 1 && esz * static_cast<size_t>(max_block_dim) <= kApplyClusterMaxSmem) {
+    if constexpr (sizeof(R) == 8)
+      return launch_apply_cluster_t<double, double>(nblocks, block_off, mat_off, tile_off, nmax, perm, mats, tinv,
+                                                    piv, N, nrhs, x, y, max_block_dim, csize, st);
+    else
+      return launch_apply_cluster_t<float, float>(nblocks, block_off, mat_off, tile_off, nmax, perm, mats32, tinv32,
+                                                  piv, N, nrhs, x, y, max_block_dim, csize, st);
+  }
   if constexpr (sizeof(R) == 8)
     return launch_apply_t<double, double>(nblocks, block_off, mat_off, nmax, perm, mats, piv, N, nrhs, x, y, work,
                                           max_block_dim, st);
@@ -320,10 +541,12 @@ cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, cons
 }
 template cudaError_t launch_precond_apply<float>(int64_t, const int64_t*, const int64_t*, int, const int*,
                                                  const double*, const float*, const int*, int64_t, int, const void*,
-                                                 void*, double*, int, cudaStream_t);
+                                                 void*, double*, int, cudaStream_t, const int64_t*, const double*,
+                                                 const float*, int);
 template cudaError_t launch_precond_apply<double>(int64_t, const int64_t*, const int64_t*, int, const int*,
                                                   const double*, const float*, const int*, int64_t, int, const void*,
-                                                  void*, double*, int, cudaStream_t);
+                                                  void*, double*, int, cudaStream_t, const int64_t*, const double*,
+                                                  const float*, int);
 
 __global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)

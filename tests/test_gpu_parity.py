@@ -227,6 +227,34 @@ def test_config1_mixed_solve_reaches_chosen_form_accuracy():
         B.celes_destroy(ctx)
 
 
+@pytest.mark.parametrize("N,L,edge", [(120, 3, 700.0), (90, 3, 450.0), (60, 4, 1e5), (33, 5, 380.0)])
+def test_preconditioner_apply_large_blocks(N, L, edge):
+    # blocks of several 32-row tiles with a ragged last tile: the cluster form
+    # of the apply (2 or 4 CTAs per block), two right-hand sides, in place and
+    # out of place, against the oracle's block solves
+    sc = synth.random_cluster(26, N + L, N, L, radius=100.0, fill=0.3, n=1.55 + 0.01j)
+    ctx = make_ctx(sc)
+    try:
+        t = mie.t_diagonal(L, sc.k, sc.radii, sc.n_rel)
+        B.celes_precond_build(ctx, edge)
+        nb, maxd, ent = B.celes_precond_stats(ctx)
+        assert maxd >= 96
+        P = precond.BlockPreconditioner(sc.positions, sc.k, L, t, edge)
+        y = synth.random_vector(26, N, (2, sc.N, sc.nmax))
+        ref = np.stack([P.apply(y[0]), P.apply(y[1])])
+        for prec, dt, tol in ((B.CELES_FP64, np.complex128, 1e-10), (B.CELES_FP32, np.complex64, 1e-5)):
+            yd = dev(y, dt)
+            xd = torch.full_like(yd, float("nan"))
+            B.celes_precond_apply(ctx, yd, xd, nrhs=2, precision=prec)
+            torch.cuda.synchronize()
+            assert rel(xd.cpu().numpy(), ref) < tol
+            B.celes_precond_apply(ctx, yd, yd, nrhs=2, precision=prec)
+            torch.cuda.synchronize()
+            assert rel(yd.cpu().numpy(), ref) < tol
+    finally:
+        B.celes_destroy(ctx)
+
+
 def test_preconditioner_apply_and_preconditioned_solve():
     sc = synth.random_cluster(25, 0, 40, 2, radius=100.0, fill=0.3, n=1.6 + 0.01j)
     ctx = make_ctx(sc)
