@@ -326,10 +326,27 @@ cudaError_t launch_precond_tile_inverse(int64_t nblocks, int64_t max_tiles, cons
   return cudaGetLastError();
 }
 
-constexpr int kApplyThreads = 256;
+constexpr int kApplyThreads = 128;
 constexpr int kApplyClusterMaxSmem = 160 * 1024;  // largest block vector of the cluster form
 
-// the CTA of cluster rank s owns tiles [s * per, min(ntile, (s + 1) * per))
+// split cluster barrier: arrive (release: this thread's earlier shared and
+// distributed-shared writes become visible to the cluster) and wait (acquire)
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// The CTA of cluster rank s owns tiles [s * per, min(ntile, (s + 1) * per)).
+// The two sweeps are one sequence of 2 ntile phases; phase p solves tile
+// p (forward, L) or 2 ntile - 1 - p (backward, U).  Its owner solves the tile
+// with the tile's explicit inverse, writes the 32 values into every CTA's
+// copy of the block vector and arrives at the cluster barrier; the other CTAs
+// arrived early and only wait.  After phase p, the owner of phase p + 1 first
+// applies the new tile column to the rows of its next tile (the only update
+// on the serial path), and defers the rest of its rows until after its own
+// broadcast; every other CTA arrives for phase p + 1 at once and then updates
+// its rows.  Updates to a row commute, so only the rows of a tile about to be
+// solved must have every earlier column applied.
 template <typename R, typename F>
 __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
     const int64_t* __restrict__ block_off, const int64_t* __restrict__ mat_off, const int64_t* __restrict__ tile_off,
@@ -356,63 +373,131 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
   Pair2<F>* v = reinterpret_cast<Pair2<F>*>(pc_smem);  // [n]: own rows (partial sums) + solved tiles
   __shared__ Pair2<F> dt[32][33];
   __shared__ Pair2<F> w[32];
+  __shared__ Pair2<F> red[kApplyThreads / 32][32];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int64_t nphase = 2 * ntile;
+  auto tile_of = [&](int64_t p) { return p < ntile ? p : nphase - 1 - p; };
+  auto owns = [&](int64_t p) {
+    if (p < 0 || p >= nphase) return false;
+    const int64_t t = tile_of(p);
+    return t >= t_lo && t < t_hi;
+  };
+  auto tb_of = [&](int64_t t) { return static_cast<int>(n - t * 32 < 32 ? n - t * 32 : 32); };
+  // stage the explicit inverse of phase p's diagonal tile (L for forward, U for backward)
+  auto stage = [&](int64_t p) {
+    const Pair2<F>* Ti = TI + tile_of(p) * 2048 + (p < ntile ? 0 : 1024);
+    for (int e = tid; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
+  };
+  // v[rows of tile tr] -= A[tile tr, tile tc] v[tile tc], all threads (4 x 32 split of the columns)
+  auto tile_update = [&](int64_t tr, int64_t tc) {
+    const int64_t rb = tr * 32, cb = tc * 32;
+    const int tbr = tb_of(tr), tbc = tb_of(tc);
+    const int part = tid >> 5;  // columns part, part + 4, ...
+    F re = 0, im = 0;
+    if (lane < tbr) {
+      for (int c = part; c < tbc; c += kApplyThreads / 32) {
+        const Pair2<F> a = A[(rb + lane) + (cb + c) * n], u = v[cb + c];
+        re += a.re * u.re - a.im * u.im;
+        im += a.re * u.im + a.im * u.re;
+      }
+    }
+    red[part][lane] = Pair2<F>{re, im};
+    __syncthreads();
+    if (tid < 32 && lane < tbr) {
+      Pair2<F> acc = v[rb + lane];
+#pragma unroll
+      for (int g = 0; g < kApplyThreads / 32; ++g) {
+        acc.re -= red[g][lane].re;
+        acc.im -= red[g][lane].im;
+      }
+      v[rb + lane] = acc;
+    }
+  };
+  // own rows (except tile `skip`) updated with the column of phase p
+  auto bulk_update = [&](int64_t p, int64_t skip) {
+    const int64_t t = tile_of(p);
+    const int64_t kb = t * 32;
+    const int tb = tb_of(t);
+    int64_t a0, a1;
+    if (p < ntile) {  // forward: rows below the tile
+      a0 = r_lo > kb + tb ? r_lo : kb + tb;
+      a1 = r_hi;
+    } else {          // backward: rows above the tile
+      a0 = r_lo;
+      a1 = r_hi < kb ? r_hi : kb;
+    }
+    const int64_t sk0 = skip >= 0 ? skip * 32 : 0, sk1 = skip >= 0 ? skip * 32 + tb_of(skip) : 0;
+    for (int64_t i = a0 + tid; i < a1; i += blockDim.x) {
+      if (i >= sk0 && i < sk1) continue;
+      v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+    }
+  };
+
   // gather own rows (the pivot permutation folded in)
-  for (int64_t t = r_lo + threadIdx.x; t < r_hi; t += blockDim.x) {
+  for (int64_t t = r_lo + tid; t < r_hi; t += blockDim.x) {
     const int64_t src = pp[t];
     const int64_t a = src / nmax;
     const int r = static_cast<int>(src - a * nmax);
     const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
     v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
   }
+  if (owns(0)) stage(0);
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  // one triangular sweep; fwd: tiles 0..ntile-1 with L, else ntile-1..0 with U
-  auto sweep = [&](bool fwd) {
-    for (int64_t step = 0; step < ntile; ++step) {
-      const int64_t k = fwd ? step : ntile - 1 - step;
-      const int64_t kb = k * 32;
-      const int tb = static_cast<int>(n - kb < 32 ? n - kb : 32);
-      const bool owner = k >= t_lo && k < t_hi;
-      if (owner) {
-        const Pair2<F>* Ti = TI + k * 2048 + (fwd ? 0 : 1024);
-        for (int e = threadIdx.x; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
-        __syncthreads();
-        if (threadIdx.x < 32) {
-          F re = 0, im = 0;
+  if (!owns(0)) cluster_arrive();
+  int64_t pending = -1;  // phase whose column update of the remaining own rows is deferred
+  int64_t pending_skip = -1;
+  for (int64_t p = 0; p < nphase; ++p) {
+    if (owns(p)) {
+      // the tile's rows have every earlier column applied; dt holds its inverse
+      const int64_t kb = tile_of(p) * 32;
+      const int tb = tb_of(tile_of(p));
+      if (tid < 32) {
+        F re = 0, im = 0;
 #pragma unroll 8
-          for (int c = 0; c < 32; ++c) {
-            if (c < tb) {
-              const Pair2<F> a = dt[c][lane], u = v[kb + c];
-              re += a.re * u.re - a.im * u.im;
-              im += a.re * u.im + a.im * u.re;
-            }
+        for (int c = 0; c < 32; ++c) {
+          if (c < tb) {
+            const Pair2<F> a = dt[c][lane], u = v[kb + c];
+            re += a.re * u.re - a.im * u.im;
+            im += a.re * u.im + a.im * u.re;
           }
-          w[lane] = Pair2<F>{re, im};
         }
-        __syncthreads();
-        // the solved tile into every CTA's copy of the block vector
-        for (int e = threadIdx.x; e < C * 32; e += blockDim.x) {
-          const int dst = e >> 5, r = e & 31;
-          if (r < tb) cluster.map_shared_rank(v, dst)[kb + r] = w[r];
-        }
+        w[lane] = Pair2<F>{re, im};
       }
-      cluster.sync();
-      // apply tile column k to own rows below (fwd) / above (back) the tile
-      const int64_t a0 = fwd ? (r_lo > kb + tb ? r_lo : kb + tb) : r_lo;
-      const int64_t a1 = fwd ? r_hi : (r_hi < kb ? r_hi : kb);
-      for (int64_t i = a0 + threadIdx.x; i < a1; i += blockDim.x) v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+      __syncthreads();
+      for (int e = tid; e < C * 32; e += blockDim.x) {
+        const int dst = e >> 5, r = e & 31;
+        if (r < tb) cluster.map_shared_rank(v, dst)[kb + r] = w[r];
+      }
+      cluster_arrive();
+      if (pending >= 0) {
+        bulk_update(pending, pending_skip);
+        pending = -1;
+      }
+    }
+    cluster_wait();  // phase p complete: its tile's values are in v
+    __syncthreads();
+    const bool same_sweep = (p + 1 < ntile) || (p >= ntile);
+    if (owns(p + 1)) {
+      stage(p + 1);
+      if (same_sweep) tile_update(tile_of(p + 1), tile_of(p));
+      __syncthreads();
+      pending = p;
+      pending_skip = tile_of(p + 1);
+    } else {
+      if (p + 1 < nphase) cluster_arrive();
+      bulk_update(p, -1);
       __syncthreads();
     }
-  };
-  sweep(true);
-  sweep(false);
-  for (int64_t t = r_lo + threadIdx.x; t < r_hi; t += blockDim.x) {
+  }
+  for (int64_t t = r_lo + tid; t < r_hi; t += blockDim.x) {
     const int64_t a = t / nmax;
     const int r = static_cast<int>(t - a * nmax);
     yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
   }
   // no CTA leaves while others may still write its shared memory
-  cluster.sync();
+  cluster_arrive();
+  cluster_wait();
 }
 
 // position -> source index of the row interchanges of each block's LU
