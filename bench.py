@@ -63,8 +63,10 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="receivers in the CPU sample (0 = auto)")
     ap.add_argument("--small-n", type=int, default=2000, help="spheres of the measured plain-FP64 comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-ensemble measurement")
-    ap.add_argument("--batched-ensembles", type=int, default=12)
-    ap.add_argument("--batched-rhs", type=int, default=4)
+    ap.add_argument("--batched-ensembles", type=int, default=64)
+    ap.add_argument("--batched-rhs", type=int, default=8)
+    ap.add_argument("--batched-scale", type=float, default=1.0,
+                    help="sphere counts of the multi-ensemble workload times this factor (1 = as stated)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess measurement")
     ap.add_argument("--no-precond", action="store_true", help="skip the block-preconditioned solve")
     ap.add_argument("--no-certify", action="store_true",
@@ -265,17 +267,28 @@ def run_reference(args, rank):
 # our arm
 # ---------------------------------------------------------------------------
 
-def run_batched(args, local_rank):
-    """Many uneven ensembles x RHS in one lockstep batched solve against the
-    same systems solved one context at a time (ensembles of the multi-ensemble
-    recipe: lmax 2..5, plane waves from a 60 degree cap; sizes scaled by 0.4
-    so the measurement takes seconds)."""
-    import torch
+def _pack_config3(index, n_rhs, scale):
+    """Worker: one multi-ensemble scene (spawn pool)."""
     import synth
+    N = None if scale >= 1.0 else max(80, int(scale * synth.config3_size(index)))
+    return synth.config3(index, n_rhs=n_rhs, N=N)
+
+
+def run_batched(args, local_rank):
+    """The multi-ensemble workload as stated: 64 ensembles (N ~ U[200, 3000],
+    lmax 2..5, lambda, R, n and fill drawn per ensemble) with 8 plane waves
+    each, solved in one lockstep batched solve (one persistent coupling launch
+    per lmax and precision for all 512 systems, the operator replayed from a
+    CUDA graph), against the same systems solved one context at a time.
+    Packings come from spawn workers on the host cores."""
+    import multiprocessing as mp
+    import torch
     from paper_1706_02145_gb300 import binding as B
-    scenes = []
-    for e in range(args.batched_ensembles):
-        scenes.append(synth.config3(e, n_rhs=args.batched_rhs, N=max(80, int(0.4 * synth.config3_size(e)))))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, host_cores())) as pool:
+        scenes = pool.starmap(_pack_config3, [(e, args.batched_rhs, args.batched_scale)
+                                              for e in range(args.batched_ensembles)])
+    t_pack = time.perf_counter() - t0
     ctxs = []
     try:
         for sc in scenes:
@@ -289,10 +302,12 @@ def run_batched(args, local_rank):
             x = torch.ones(n, dtype=torch.complex64, device=f"cuda:{local_rank}")
             y = torch.empty_like(x)
             B.celes_batch_master_matvec(bt, x, y, precision=B.CELES_FP32)  # graph capture, warm-up
-            reps = 5
+            reps = 3
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
                 B.celes_batch_master_matvec(bt, x, y, precision=B.CELES_FP32)
+            torch.cuda.synchronize()
             t_mv = (time.perf_counter() - t0) / reps
             pairs = sum(sc.N * (sc.N - 1) * len(sc.incidents) for sc in scenes)
             code, infos = B.celes_batch_solve(bt, len(ctxs), TOL, mode=B.CELES_SOLVE_MIXED, restart=30,
@@ -300,20 +315,26 @@ def run_batched(args, local_rank):
             t_batch = max(i["seconds"] for i in infos)
             res_batch = max(i["residual"] for i in infos)
             its_batch = max(i["iterations"] for i in infos)
+            b_batch = [B.celes_get_coefficients(c) for c in ctxs]
         finally:
             B.celes_batch_destroy(bt)
-        t_one, res_one = 0.0, 0.0
-        for c in ctxs:
+        t_one, res_one, err = 0.0, 0.0, 0.0
+        for c, bb in zip(ctxs, b_batch):
             info = B.celes_solve(c, TOL, mode=B.CELES_SOLVE_MIXED, restart=30, use_precond=False,
                                  raise_on_noconv=False)
             t_one += info["seconds"]
             res_one = max(res_one, info["residual"])
+            b1 = B.celes_get_coefficients(c)
+            err = max(err, float(np.linalg.norm(bb - b1) / np.linalg.norm(b1)))
         return {"ensembles": len(scenes), "rhs_each": args.batched_rhs, "systems": len(scenes) * args.batched_rhs,
+                "size_scale": args.batched_scale, "pack_s": t_pack,
                 "N_range": [min(sc.N for sc in scenes), max(sc.N for sc in scenes)],
-                "lmax_values": sorted({sc.lmax for sc in scenes}),
+                "spheres_total": int(sum(sc.N for sc in scenes)),
+                "lmax_counts": {str(L): sum(1 for sc in scenes if sc.lmax == L) for L in range(1, 6)},
                 "operator_fp32_ms": t_mv * 1e3, "operator_couplings_per_s": pairs / t_mv,
                 "batched_solve_s": t_batch, "batched_max_iterations": its_batch, "batched_max_residual": res_batch,
                 "one_by_one_solve_s": t_one, "one_by_one_max_residual": res_one, "speedup": t_one / t_batch,
+                "batched_vs_one_by_one_max_rel_l2": err,
                 "note": "mixed FP32/FP64 GMRES(30) to 1e-6, no preconditioner, first iterate T a, both forms"}
     finally:
         for c in ctxs:

@@ -326,7 +326,7 @@ cudaError_t launch_precond_tile_inverse(int64_t nblocks, int64_t max_tiles, cons
   return cudaGetLastError();
 }
 
-constexpr int kApplyThreads = 128;
+constexpr int kApplyThreads = 256;
 constexpr int kApplyClusterMaxSmem = 160 * 1024;  // largest block vector of the cluster form
 
 // split cluster barrier: arrive (release: this thread's earlier shared and
@@ -336,17 +336,20 @@ __device__ __forceinline__ void cluster_arrive() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-// The CTA of cluster rank s owns tiles [s * per, min(ntile, (s + 1) * per)).
-// The two sweeps are one sequence of 2 ntile phases; phase p solves tile
-// p (forward, L) or 2 ntile - 1 - p (backward, U).  Its owner solves the tile
-// with the tile's explicit inverse, writes the 32 values into every CTA's
-// copy of the block vector and arrives at the cluster barrier; the other CTAs
-// arrived early and only wait.  After phase p, the owner of phase p + 1 first
-// applies the new tile column to the rows of its next tile (the only update
-// on the serial path), and defers the rest of its rows until after its own
-// broadcast; every other CTA arrives for phase p + 1 at once and then updates
-// its rows.  Updates to a row commute, so only the rows of a tile about to be
-// solved must have every earlier column applied.
+// Tiles are dealt round robin: tile t belongs to the CTA of cluster rank
+// t mod C.  The two sweeps are one sequence of 2 ntile phases; phase p solves
+// tile p (forward, L) or 2 ntile - 1 - p (backward, U).  Its owner multiplies
+// the tile's rows by the explicit inverse of the diagonal tile, writes the 32
+// values into every CTA's copy of the block vector and arrives at the
+// cluster barrier; every other CTA arrived early and only waits.  While
+// waiting for phase p, the owner of phase p + 1 already stages that phase's
+// tile inverse and the 32 x 32 block of the factor that couples the two tiles
+// (neither depends on the vector), so its serial path after the barrier is
+// two small products from shared memory.  The rest of a CTA's rows take the
+// new column only after its own broadcast; since ownership rotates, that bulk
+// work overlaps the next C - 1 phases of the other CTAs.  Updates to a row
+// commute, so only the rows of a tile about to be solved must have every
+// earlier column applied.
 template <typename R, typename F>
 __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
     const int64_t* __restrict__ block_off, const int64_t* __restrict__ mat_off, const int64_t* __restrict__ tile_off,
@@ -361,95 +364,77 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
   const int64_t s0 = block_off[q];
   const int64_t n = (block_off[q + 1] - s0) * nmax;
   const int64_t ntile = (n + 31) / 32;
-  const int64_t per = (ntile + C - 1) / C;
-  const int64_t t_lo = s * per < ntile ? s * per : ntile;
-  const int64_t t_hi = (s + 1) * per < ntile ? (s + 1) * per : ntile;
-  const int64_t r_lo = t_lo * 32, r_hi = t_hi * 32 < n ? t_hi * 32 : n;
   const Pair2<F>* A = mats + mat_off[q];
   const Pair2<F>* TI = tinv + tile_off[q];
   const int* pp = pivperm + s0 * nmax;
   const Pair2<R>* xr = x + (int64_t)rhs * N * nmax;
   Pair2<R>* yr = y + (int64_t)rhs * N * nmax;
   Pair2<F>* v = reinterpret_cast<Pair2<F>*>(pc_smem);  // [n]: own rows (partial sums) + solved tiles
-  __shared__ Pair2<F> dt[32][33];
+  __shared__ Pair2<F> dt[32][33];  // inverse of the next diagonal tile, dt[col][row]
+  __shared__ Pair2<F> ls[32][33];  // factor block coupling the next tile to the current one, ls[col][row]
   __shared__ Pair2<F> w[32];
   __shared__ Pair2<F> red[kApplyThreads / 32][32];
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = kApplyThreads / 32;
   const int64_t nphase = 2 * ntile;
   auto tile_of = [&](int64_t p) { return p < ntile ? p : nphase - 1 - p; };
-  auto owns = [&](int64_t p) {
-    if (p < 0 || p >= nphase) return false;
-    const int64_t t = tile_of(p);
-    return t >= t_lo && t < t_hi;
-  };
+  auto owns = [&](int64_t p) { return p >= 0 && p < nphase && (tile_of(p) % C) == s; };
   auto tb_of = [&](int64_t t) { return static_cast<int>(n - t * 32 < 32 ? n - t * 32 : 32); };
-  // stage the explicit inverse of phase p's diagonal tile (L for forward, U for backward)
-  auto stage = [&](int64_t p) {
-    const Pair2<F>* Ti = TI + tile_of(p) * 2048 + (p < ntile ? 0 : 1024);
-    for (int e = tid; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
-  };
-  // v[rows of tile tr] -= A[tile tr, tile tc] v[tile tc], all threads (4 x 32 split of the columns)
-  auto tile_update = [&](int64_t tr, int64_t tc) {
-    const int64_t rb = tr * 32, cb = tc * 32;
-    const int tbr = tb_of(tr), tbc = tb_of(tc);
-    const int part = tid >> 5;  // columns part, part + 4, ...
-    F re = 0, im = 0;
-    if (lane < tbr) {
-      for (int c = part; c < tbc; c += kApplyThreads / 32) {
-        const Pair2<F> a = A[(rb + lane) + (cb + c) * n], u = v[cb + c];
-        re += a.re * u.re - a.im * u.im;
-        im += a.re * u.im + a.im * u.re;
-      }
-    }
-    red[part][lane] = Pair2<F>{re, im};
-    __syncthreads();
-    if (tid < 32 && lane < tbr) {
-      Pair2<F> acc = v[rb + lane];
-#pragma unroll
-      for (int g = 0; g < kApplyThreads / 32; ++g) {
-        acc.re -= red[g][lane].re;
-        acc.im -= red[g][lane].im;
-      }
-      v[rb + lane] = acc;
-    }
-  };
-  // own rows (except tile `skip`) updated with the column of phase p
-  auto bulk_update = [&](int64_t p, int64_t skip) {
+  // stage phase p's tile inverse and, when phase p - 1 is of the same sweep,
+  // the factor block A[tile(p) rows, tile(p - 1) columns]
+  auto prefetch = [&](int64_t p) {
     const int64_t t = tile_of(p);
-    const int64_t kb = t * 32;
-    const int tb = tb_of(t);
-    int64_t a0, a1;
-    if (p < ntile) {  // forward: rows below the tile
-      a0 = r_lo > kb + tb ? r_lo : kb + tb;
-      a1 = r_hi;
-    } else {          // backward: rows above the tile
-      a0 = r_lo;
-      a1 = r_hi < kb ? r_hi : kb;
+    const Pair2<F>* Ti = TI + t * 2048 + (p < ntile ? 0 : 1024);
+    for (int e = tid; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
+    const bool same = p > 0 && ((p < ntile) == (p - 1 < ntile));
+    if (same) {
+      const int64_t rb = t * 32, cb = tile_of(p - 1) * 32;
+      const int tbr = tb_of(t), tbc = tb_of(tile_of(p - 1));
+      for (int e = tid; e < 1024; e += blockDim.x) {
+        const int c = e >> 5, r = e & 31;
+        ls[c][r] = (r < tbr && c < tbc) ? A[(rb + r) + (cb + c) * n] : Pair2<F>{0, 0};
+      }
     }
-    const int64_t sk0 = skip >= 0 ? skip * 32 : 0, sk1 = skip >= 0 ? skip * 32 + tb_of(skip) : 0;
-    for (int64_t i = a0 + tid; i < a1; i += blockDim.x) {
-      if (i >= sk0 && i < sk1) continue;
-      v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+  };
+  // own rows of tiles beyond phase p's tile (in its sweep), except tile `skip`,
+  // updated with the column of phase p; one warp per tile, one lane per row
+  auto bulk_update = [&](int64_t p, int64_t skip) {
+    const int64_t kt = tile_of(p);
+    const int64_t kb = kt * 32;
+    const int tb = tb_of(kt);
+    const bool fwd = p < ntile;
+    // owned tiles after kt (fwd) or before kt (back), in order of distance
+    const int64_t first = fwd ? kt + 1 + ((s - (kt + 1) % C) % C + C) % C : kt - 1 - (((kt - 1) % C - s) % C + C) % C;
+    for (int64_t j = wid;; j += NW) {
+      const int64_t t = fwd ? first + j * C : first - j * C;
+      if (fwd ? t >= ntile : t < 0) break;
+      if (t == skip) continue;
+      if (lane < tb_of(t)) {
+        const int64_t i = t * 32 + lane;
+        v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
+      }
     }
   };
 
   // gather own rows (the pivot permutation folded in)
-  for (int64_t t = r_lo + tid; t < r_hi; t += blockDim.x) {
-    const int64_t src = pp[t];
-    const int64_t a = src / nmax;
-    const int r = static_cast<int>(src - a * nmax);
-    const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
-    v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
+  for (int64_t t0 = s; t0 < ntile; t0 += C) {
+    for (int r = tid; r < tb_of(t0); r += blockDim.x) {
+      const int64_t t = t0 * 32 + r;
+      const int64_t src = pp[t];
+      const int64_t a = src / nmax;
+      const int rr = static_cast<int>(src - a * nmax);
+      const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + rr];
+      v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
+    }
   }
-  if (owns(0)) stage(0);
+  if (owns(0)) prefetch(0);
   __syncthreads();
   if (!owns(0)) cluster_arrive();
-  int64_t pending = -1;  // phase whose column update of the remaining own rows is deferred
-  int64_t pending_skip = -1;
+  int64_t pending = -1, pending_skip = -1;
   for (int64_t p = 0; p < nphase; ++p) {
     if (owns(p)) {
-      // the tile's rows have every earlier column applied; dt holds its inverse
+      // rows of the tile: every earlier column applied; dt holds the inverse
       const int64_t kb = tile_of(p) * 32;
       const int tb = tb_of(tile_of(p));
       if (tid < 32) {
@@ -475,12 +460,35 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
         pending = -1;
       }
     }
-    cluster_wait();  // phase p complete: its tile's values are in v
+    const bool next = owns(p + 1);
+    if (next) prefetch(p + 1);  // independent of the vector: overlaps the wait
+    cluster_wait();             // phase p complete: its tile's values are in v
     __syncthreads();
-    const bool same_sweep = (p + 1 < ntile) || (p >= ntile);
-    if (owns(p + 1)) {
-      stage(p + 1);
-      if (same_sweep) tile_update(tile_of(p + 1), tile_of(p));
+    if (next) {
+      const bool same = (p + 1 < ntile) || (p >= ntile);
+      if (same) {
+        // rows of tile(p + 1) -= ls * v[tile(p)], columns split over the warps
+        const int64_t rb = tile_of(p + 1) * 32, cb = tile_of(p) * 32;
+        F re = 0, im = 0;
+        for (int c = wid; c < 32; c += NW) {
+          const Pair2<F> a = ls[c][lane], u = v[cb + (c < tb_of(tile_of(p)) ? c : 0)];
+          if (c < tb_of(tile_of(p))) {
+            re += a.re * u.re - a.im * u.im;
+            im += a.re * u.im + a.im * u.re;
+          }
+        }
+        red[wid][lane] = Pair2<F>{re, im};
+        __syncthreads();
+        if (tid < 32 && lane < tb_of(tile_of(p + 1))) {
+          Pair2<F> acc = v[rb + lane];
+#pragma unroll
+          for (int g = 0; g < NW; ++g) {
+            acc.re -= red[g][lane].re;
+            acc.im -= red[g][lane].im;
+          }
+          v[rb + lane] = acc;
+        }
+      }
       __syncthreads();
       pending = p;
       pending_skip = tile_of(p + 1);
@@ -490,10 +498,13 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
       __syncthreads();
     }
   }
-  for (int64_t t = r_lo + tid; t < r_hi; t += blockDim.x) {
-    const int64_t a = t / nmax;
-    const int r = static_cast<int>(t - a * nmax);
-    yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
+  for (int64_t t0 = s; t0 < ntile; t0 += C) {
+    for (int r = tid; r < tb_of(t0); r += blockDim.x) {
+      const int64_t t = t0 * 32 + r;
+      const int64_t a = t / nmax;
+      const int rr = static_cast<int>(t - a * nmax);
+      yr[(int64_t)perm[s0 + a] * nmax + rr] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
+    }
   }
   // no CTA leaves while others may still write its shared memory
   cluster_arrive();

@@ -21,8 +21,9 @@ Stillinger and MSTM packings, which are not available here):
   at the centre of the illuminated (z = z_min) face, x-polarised.
 * ``config3``  ensemble ``index`` of 64: N ~ U[200, 3000], lmax ~ U{2..5},
   lambda ~ U[400, 800] nm, R ~ U[80, 200] nm (one radius per ensemble), real
-  n ~ U[1.45, 2.0], fill ~ U[0.1, 0.35] in a cube, 8 plane waves with
-  directions on a Fibonacci lattice of the cap beta <= 60 deg, polarisation 2.
+  n ~ U[1.45, 2.0], fill ~ U[0.1, 0.35] in a cube (FCC lattice plus hard-
+  sphere Monte Carlo above 0.3), 8 plane waves with directions on a Fibonacci
+  lattice of the cap beta <= 60 deg, polarisation 2.
 * ``config5``  N spheres (default 100 000), R = 130 nm, n = 1.52, lambda =
   550 nm, lmax = 3, slab of thickness 4 um at fill 0.25 (square footprint from
   N and the fill), Gaussian beam w = 5 um.
@@ -211,14 +212,15 @@ def config3_size(index: int) -> int:
 
 
 def config3(index: int, n_rhs: int = 8, N: Optional[int] = None, lmax: Optional[int] = None,
-            max_tries: int = 2_000_000) -> Scene:
+            max_tries: int = 2_000_000, sweeps: int = 200) -> Scene:
     """Multi-ensemble ``index``: N ~ U[200, 3000], lmax ~ U{2..5}, lambda, R, n
     and fill drawn per ensemble; monodisperse spheres in a cube; ``n_rhs``
-    plane waves on a Fibonacci cap beta <= 60 deg.  The walls exclude a shell
-    of one radius, so for small N a fill near 0.35 can exceed what random
-    sequential addition packs: then the cube grows in 3 % steps (a new pass
-    from the same seed each time) until the spheres fit, and the ensemble's
-    fill is lower than drawn."""
+    plane waves on a Fibonacci cap beta <= 60 deg.  Fills above 0.3 use an FCC
+    lattice with hard-sphere Monte-Carlo sweeps (``fcc_shaken_cube``; random
+    sequential addition slows sharply on its way to jamming), others random
+    sequential addition.  Should addition give up (its try budget), the cube
+    grows in 3 % steps (a new pass from the same seed each time) until the
+    spheres fit, and that ensemble's fill is lower than drawn."""
     sides = []
     for grow in range(60):
         rng = rng_for(3, index)
@@ -231,12 +233,15 @@ def config3(index: int, n_rhs: int = 8, N: Optional[int] = None, lmax: Optional[
         def sampler(rng, r, m, side=side):
             return rng.uniform(r, side - r, size=(m, 3))
 
-        try:
-            pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side),
-                                             max_tries=max_tries if grow == 0 else 400 * N)
-        except RuntimeError:
-            sides.append(side)
-            continue
+        if fill > 0.3 and grow == 0:
+            pos = fcc_shaken_cube(rng, N, R, side, sweeps=sweeps)
+        else:
+            try:
+                pos = random_sequential_addition(rng, radii, sampler, (0, 0, 0), (side, side, side),
+                                                 max_tries=max_tries if grow == 0 else 400 * N)
+            except RuntimeError:
+                sides.append(side)
+                continue
         betas, alphas = fibonacci_cap(n_rhs, np.deg2rad(60.0))
         incs = [Incident("plane", beta=float(b), alpha=float(a), pol=2) for b, a in zip(betas, alphas)]
         fill_eff = N * 4.0 / 3.0 * np.pi * R ** 3 / side ** 3

@@ -73,17 +73,29 @@ def test_config3_sizes_of_all_64_ensembles():
     assert all(200 <= n <= 3000 for n in sizes) and len(set(sizes)) > 50
 
 
-def test_config3_grows_the_cube_when_the_drawn_fill_cannot_be_packed():
-    """Ensemble 17 at 300 spheres draws a fill that random sequential addition
-    cannot reach inside the walls; with a small try budget the first pass
-    gives up at once and a larger cube is used, from the same seed."""
-    sc = synth.config3(17, N=300, max_tries=20_000)
-    assert sc.N == 300 and _disjoint(sc)
-    side = sc.positions.max() + sc.radii[0]
+def test_config3_dense_ensembles_keep_their_drawn_fill():
+    """Ensemble 17 draws fill 0.34: it is packed from an FCC lattice shaken by
+    hard-sphere Monte Carlo, inside the walls of the cube of exactly that
+    fill, disjoint and reproducible."""
+    sc = synth.config3(17, N=300, sweeps=30)
     drawn = synth._config3_draw(synth.rng_for(3, 17))[5]
-    assert np.sum(4.0 / 3.0 * np.pi * sc.radii ** 3) / side ** 3 < drawn
-    again = synth.config3(17, N=300, max_tries=20_000)
+    assert drawn > 0.3
+    side = (np.sum(4.0 / 3.0 * np.pi * sc.radii ** 3) / drawn) ** (1.0 / 3.0)
+    assert np.all(sc.positions >= sc.radii[0] - 1e-9) and np.all(sc.positions <= side - sc.radii[0] + 1e-9)
+    assert sc.N == 300 and _disjoint(sc)
+    again = synth.config3(17, N=300, sweeps=30)
     assert np.array_equal(sc.positions, again.positions)
+
+
+def test_config3_grows_the_cube_when_addition_gives_up():
+    """With a try budget too small for random sequential addition, the cube
+    grows (from the same seed) until the spheres fit: the fill is lower."""
+    sc = synth.config3(12, N=300, max_tries=300)
+    drawn = synth._config3_draw(synth.rng_for(3, 12))[5]
+    assert drawn <= 0.3
+    side = sc.positions.max() + sc.radii[0]
+    assert sc.N == 300 and _disjoint(sc)
+    assert np.sum(4.0 / 3.0 * np.pi * sc.radii ** 3) / side ** 3 < drawn
 
 
 @pytest.mark.parametrize("fill", [0.25, 0.38, 0.4])
