@@ -67,6 +67,13 @@ typedef struct {
   int check_overlap;    /* reject overlapping spheres (default 1) */
   int chunks;           /* source chunks of the coupling kernel; 0 = automatic */
   int kernel;           /* celes_kernel: coupling-kernel variant (default AUTO) */
+  int autotune;         /* 1 (default): the first coupling product in each precision times the
+                           candidate launch shapes and source-chunk counts of the coupling kernel
+                           on this problem (cached per device, lmax, precision and size class) and
+                           keeps the fastest; it synchronises, so make that first product before
+                           any stream capture.  0: the built-in shape, about eight waves of chunks */
+  int variant;          /* -1 (default): as autotune decides; 0 or 1: force the FP32 launch shape
+                           (0 = built-in, 1 = the alternative); FP64 always uses the built-in one */
 } celes_options;
 
 typedef enum { CELES_PLANE_WAVE = 0, CELES_GAUSSIAN_BEAM = 1 } celes_incident_kind;
@@ -161,6 +168,13 @@ int celes_master_matvec(celes_ctx* ctx, const void* x, void* y, int nrhs, int pr
  * each diagonal block of M in FP64 and LU-factor it with partial pivoting on
  * the GPU.  Replaces any earlier preconditioner. */
 int celes_precond_build(celes_ctx* ctx, double cuboid_edge);
+
+/* Launch shape the context's coupling kernel uses in `precision`: variant
+ * (0 built-in, 1 alternative FP32 shape), source chunks per product and, if
+ * the autotuner chose it, the timed duration of the winning candidate (ms; 0
+ * otherwise).  CELES_ESTATE before the first coupling product in that
+ * precision.  Measurement support; the paper has no counterpart. */
+int celes_coupling_shape(const celes_ctx* ctx, int precision, int* variant, int* chunks, double* ms);
 
 /* Size of the built block preconditioner: number of blocks (cuboids that
  * hold spheres), largest block dimension (unknowns) and the total number of

@@ -50,7 +50,7 @@ CELES_KERNEL_RTR = 2
 
 class celes_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("check_overlap", ctypes.c_int), ("chunks", ctypes.c_int),
-                ("kernel", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("variant", ctypes.c_int)]
 
 
 class celes_incident(ctypes.Structure):
@@ -79,6 +79,8 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 # (name, restype, argtypes) of every exported symbol of include/celes.h
 SIGNATURES = [
+    ("celes_coupling_shape", ctypes.c_int, [_c_ctx_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     ("celes_precond_stats", ctypes.c_int, [_c_ctx_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
     ("celes_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -235,11 +237,12 @@ def _stream(s):
 # ---------------------------------------------------------------------------
 
 def celes_create(positions, radii, n_i, n0, k0, lmax, device=0, check_overlap=True, chunks=0,
-                 kernel=CELES_KERNEL_AUTO):
+                 kernel=CELES_KERNEL_AUTO, autotune=True, variant=-1):
     pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1, 3)
     rad = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
     ni = np.ascontiguousarray(np.asarray(n_i, dtype=np.complex128).reshape(-1)).view(np.float64)
-    opt = celes_options(int(device), int(bool(check_overlap)), int(chunks), int(kernel))
+    opt = celes_options(int(device), int(bool(check_overlap)), int(chunks), int(kernel), int(bool(autotune)),
+                        int(variant))
     ctx = _c_ctx_p()
     code = load().celes_create(ctypes.byref(ctx), pos.shape[0], _dptr(pos), _dptr(rad), _dptr(ni),
                                float(n0), float(k0), int(lmax), ctypes.byref(opt))
@@ -287,6 +290,13 @@ def celes_precond_apply(ctx, x, y, nrhs=1, precision=CELES_FP64, stream=None):
     _ctx_vec_checks(ctx, x, y, nrhs, precision)
     return _check(load().celes_precond_apply(ctx, _devptr(x), _devptr(y), int(nrhs), int(precision),
                                              _stream(stream)), ctx)
+
+
+def celes_coupling_shape(ctx, precision):
+    """(variant, chunks, tuned ms) of the context's coupling kernel in `precision`."""
+    v, ch, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().celes_coupling_shape(ctx, int(precision), ctypes.byref(v), ctypes.byref(ch), ctypes.byref(ms)), ctx)
+    return v.value, ch.value, ms.value
 
 
 def celes_precond_stats(ctx):

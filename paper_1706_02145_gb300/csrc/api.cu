@@ -15,7 +15,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <tuple>
@@ -37,6 +39,17 @@ namespace celes {
   int coupling_rtr_slots_##LL(int precision);                                                              \
   long long coupling_rtr_flops_##LL();                                                                     \
   int coupling_terms_export_##LL(int* idx, double* val, int cap);
+#define CELES_DECLARE_ALT(LL)                                                                              \
+  cudaError_t launch_coupling_rtr_alt_##LL(int64_t N, const void* pos, const void* x, void* partial,       \
+                                           double k, int chunks, cudaStream_t st);                         \
+  int coupling_rtr_alt_rpb_##LL();                                                                         \
+  int coupling_rtr_alt_slots_##LL();
+CELES_DECLARE_ALT(1)
+CELES_DECLARE_ALT(2)
+CELES_DECLARE_ALT(3)
+CELES_DECLARE_ALT(4)
+CELES_DECLARE_ALT(5)
+#undef CELES_DECLARE_ALT
 CELES_DECLARE(1)
 CELES_DECLARE(2)
 CELES_DECLARE(3)
@@ -64,6 +77,45 @@ cudaError_t launch_coupling_rtr(int L, int precision, int64_t N, const void* pos
     case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st);
     case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st);
     default: return cudaErrorInvalidValue;
+  }
+}
+int coupling_rtr_receivers_per_block(int L, int precision);
+int coupling_rtr_slots(int L, int precision);
+
+// launch shape `variant` (0: Config, 1: ConfigAlt, FP32 only)
+cudaError_t launch_coupling_rtr_v(int L, int precision, int variant, int64_t N, const void* pos, const void* x,
+                                  void* partial, double k, int chunks, cudaStream_t st) {
+  if (variant == 0 || precision == CELES_FP64)
+    return launch_coupling_rtr(L, precision, N, pos, x, partial, k, chunks, st);
+  switch (L) {
+    case 1: return launch_coupling_rtr_alt_1(N, pos, x, partial, k, chunks, st);
+    case 2: return launch_coupling_rtr_alt_2(N, pos, x, partial, k, chunks, st);
+    case 3: return launch_coupling_rtr_alt_3(N, pos, x, partial, k, chunks, st);
+    case 4: return launch_coupling_rtr_alt_4(N, pos, x, partial, k, chunks, st);
+    case 5: return launch_coupling_rtr_alt_5(N, pos, x, partial, k, chunks, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+int coupling_rtr_rpb_v(int L, int precision, int variant) {
+  if (variant == 0 || precision == CELES_FP64) return coupling_rtr_receivers_per_block(L, precision);
+  switch (L) {
+    case 1: return coupling_rtr_alt_rpb_1();
+    case 2: return coupling_rtr_alt_rpb_2();
+    case 3: return coupling_rtr_alt_rpb_3();
+    case 4: return coupling_rtr_alt_rpb_4();
+    case 5: return coupling_rtr_alt_rpb_5();
+    default: return 0;
+  }
+}
+int coupling_rtr_slots_v(int L, int precision, int variant) {
+  if (variant == 0 || precision == CELES_FP64) return coupling_rtr_slots(L, precision);
+  switch (L) {
+    case 1: return coupling_rtr_alt_slots_1();
+    case 2: return coupling_rtr_alt_slots_2();
+    case 3: return coupling_rtr_alt_slots_3();
+    case 4: return coupling_rtr_alt_slots_4();
+    case 5: return coupling_rtr_alt_slots_5();
+    default: return 0;
   }
 }
 int coupling_rtr_receivers_per_block(int L, int precision) {
@@ -158,6 +210,12 @@ struct celes_ctx {
   double n0 = 1.0, k0 = 0.0, k = 0.0;
   int chunks_opt = 0;
   int kernel = CELES_KERNEL_AUTO;
+  int autotune = 1;
+  // launch shape of the coupling kernel per precision (FP64, FP32): -1 until
+  // the first product picks it (autotuner) or the default is taken
+  int tune_variant[2] = {-1, -1};
+  int tune_chunks[2] = {0, 0};
+  double tune_ms[2] = {0.0, 0.0};
   DevBuf pos, radii, nrel, tq, tq32, tdiag;
   int nrhs = 0;
   std::vector<celes_incident> incidents;  // descriptors of the current RHS
@@ -256,6 +314,100 @@ int auto_chunks(const celes_ctx* c, int precision) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ch, 256)));
 }
 
+// ---- autotuner of the coupling kernel's launch shape ----------------------
+// Candidates: the compile-time shape (Config, and for FP32 ConfigAlt) times
+// the number of source chunks (about 4, 8 or 16 waves of resident CTAs).
+// Each is timed with CUDA events on the context's own positions (the first
+// 20 000 spheres of larger problems) and the fastest kept, once per (device,
+// lmax, precision, log2 N) for the whole process.
+struct TuneKey {
+  int dev, L, prec, bucket;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, L, prec, bucket) < std::tie(o.dev, o.L, o.prec, o.bucket);
+  }
+};
+struct TuneVal {
+  int variant = 0;
+  double waves = 8.0;
+  double ms = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+int chunks_for(const celes_ctx* c, int64_t N, int precision, int variant, double waves) {
+  const int rpb = coupling_rtr_rpb_v(c->L, precision, variant);
+  const int64_t rb = (N + rpb - 1) / rpb;
+  const int slots = coupling_rtr_slots_v(c->L, precision, variant);
+  const double target = waves * (slots > 0 ? slots : 2 * device_sms());
+  int64_t ch = static_cast<int64_t>(std::ceil(target / static_cast<double>(rb)));
+  ch = std::min<int64_t>(ch, std::max<int64_t>(1, N / 64));
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ch, 256)));
+}
+
+int autotune(celes_ctx* c, int precision, const void* x, cudaStream_t st) {
+  const int pi = precision == CELES_FP64 ? 0 : 1;
+  const int64_t Nt = std::min<int64_t>(c->N, 20000);
+  int bucket = 0;
+  while ((int64_t(1) << (bucket + 1)) <= c->N) ++bucket;
+  const TuneKey key{c->device, c->L, precision, bucket};
+  TuneVal best;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      best = it->second;
+      have = true;
+    }
+  }
+  if (!have) {
+    const size_t elem = precision == CELES_FP64 ? 16 : 8;
+    const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
+    const int nvar = precision == CELES_FP64 ? 1 : 2;
+    const double waves[3] = {4.0, 8.0, 16.0};
+    int maxch = 1;
+    for (int v = 0; v < nvar; ++v)
+      for (double w : waves) maxch = std::max(maxch, chunks_for(c, Nt, precision, v, w));
+    CK(c->partial.ensure(per * std::max(maxch, 1)), "coupling scratch");
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "event");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return cuda_fail(c, cudaErrorMemoryAllocation, "event");
+    }
+    best.ms = 1e300;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
+      for (double w : waves) {
+        const int ch = chunks_for(c, Nt, precision, v, w);
+        // one untimed launch (first use of the shape on this device), then one timed
+        e = launch_coupling_rtr_v(c->L, precision, v, Nt, c->pos.p, x, c->partial.p, c->k, ch, st);
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) e = launch_coupling_rtr_v(c->L, precision, v, Nt, c->pos.p, x, c->partial.p, c->k, ch, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) break;
+        if (ms < best.ms) {
+          best.ms = ms;
+          best.variant = v;
+          best.waves = w;
+        }
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  c->tune_variant[pi] = best.variant;
+  c->tune_chunks[pi] = chunks_for(c, c->N, precision, best.variant, best.waves);
+  c->tune_ms[pi] = best.ms;
+  return CELES_OK;
+}
+
 // coupling (mode 0: y = W x) or master (mode 1: y = x - T W x) products
 int prof_begin(celes_ctx* c, cudaStream_t st, celes_ctx::Rec& r, int which) {
   r.which = which;
@@ -273,7 +425,21 @@ int prof_begin(celes_ctx* c, cudaStream_t st, celes_ctx::Rec& r, int which) {
 }
 
 int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision, int mode, cudaStream_t st) {
-  const int chunks = auto_chunks(c, precision);
+  const int pi = precision == CELES_FP64 ? 0 : 1;
+  if (c->tune_chunks[pi] == 0) {
+    const bool rtr = use_rtr(c, precision);
+    if (c->tune_variant[pi] < 0 && c->autotune && c->chunks_opt == 0 && rtr) {
+      const int s = autotune(c, precision, x, st);
+      if (s) return s;
+    } else {
+      if (c->tune_variant[pi] < 0) c->tune_variant[pi] = 0;
+      c->tune_chunks[pi] = c->chunks_opt > 0 ? c->chunks_opt
+                           : rtr             ? chunks_for(c, c->N, precision, c->tune_variant[pi], 8.0)
+                                             : auto_chunks(c, precision);
+    }
+  }
+  const int variant = c->tune_variant[pi];
+  const int chunks = c->tune_chunks[pi];
   const size_t elem = precision == CELES_FP64 ? 16 : 8;
   const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
   CK(c->partial.ensure(per * chunks), "coupling scratch");
@@ -286,7 +452,7 @@ int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision
       if (s) return s;
     }
     if (use_rtr(c, precision))
-      CK(launch_coupling_rtr(c->L, precision, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st),
+      CK(launch_coupling_rtr_v(c->L, precision, variant, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st),
          "coupling kernel");
     else
       CK(launch_coupling_partial(c->L, precision, c->N, c->pos.p, xr, c->partial.p, c->k, chunks, st),
@@ -357,6 +523,13 @@ extern "C" int celes_create(celes_ctx** out, int64_t N, const double* positions,
   c->device = opt ? opt->device : 0;
   c->chunks_opt = opt ? opt->chunks : 0;
   c->kernel = opt ? opt->kernel : CELES_KERNEL_AUTO;
+  c->autotune = opt ? opt->autotune : 1;
+  if (opt && opt->variant >= 0) {
+    // a forced launch shape (tests and measurements); the chunks as usual
+    if (opt->variant > 1) return CELES_EINVAL;
+    c->tune_variant[0] = 0;
+    c->tune_variant[1] = opt->variant;
+  }
   if (c->kernel < CELES_KERNEL_AUTO || c->kernel > CELES_KERNEL_RTR) return CELES_EINVAL;
   const int check_overlap = opt ? opt->check_overlap : 1;
   c->N = N;
@@ -697,6 +870,16 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
   c->mat_entries = moff[nb];
   c->max_block_dim = static_cast<int>(max_dim);
   c->has_precond = true;
+  return CELES_OK;
+}
+
+extern "C" int celes_coupling_shape(const celes_ctx* c, int precision, int* variant, int* chunks, double* ms) {
+  if (!c || (precision != CELES_FP64 && precision != CELES_FP32)) return CELES_EINVAL;
+  const int pi = precision == CELES_FP64 ? 0 : 1;
+  if (c->tune_chunks[pi] == 0) return CELES_ESTATE;
+  if (variant) *variant = c->tune_variant[pi];
+  if (chunks) *chunks = c->tune_chunks[pi];
+  if (ms) *ms = c->tune_ms[pi];
   return CELES_OK;
 }
 

@@ -1,0 +1,6 @@
+// Alternative FP32 coupling-kernel shape for lmax = 3 (an autotuner candidate).
+#include "coupling_launch.cuh"
+
+namespace celes {
+CELES_INSTANTIATE_RTR_ALT(3)
+}  // namespace celes

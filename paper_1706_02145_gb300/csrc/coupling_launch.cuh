@@ -115,6 +115,15 @@ long long rtr_flops_per_pair_t() {
   return f;
 }
 
+// the alternative FP32 shape (ConfigAlt), in a translation unit of its own
+#define CELES_INSTANTIATE_RTR_ALT(LL)                                                                      \
+  cudaError_t launch_coupling_rtr_alt_##LL(int64_t N, const void* pos, const void* x, void* partial,       \
+                                           double k, int chunks, cudaStream_t st) {                        \
+    return rtr::launch_partial<LL, float, rtr::ConfigAlt<LL, float>>(N, pos, x, partial, k, chunks, st);   \
+  }                                                                                                         \
+  int coupling_rtr_alt_rpb_##LL() { return rtr::ConfigAlt<LL, float>::BLOCK; }                             \
+  int coupling_rtr_alt_slots_##LL() { return rtr::resident_slots<LL, float, rtr::ConfigAlt<LL, float>>(); }
+
 #define CELES_INSTANTIATE_COUPLING(LL, FP64_UNROLLED)                                                       \
   cudaError_t launch_coupling_partial_##LL(int precision, int64_t N, const void* pos, const void* x,       \
                                             void* partial, double k, int chunks, cudaStream_t st) {        \

@@ -699,6 +699,17 @@ struct Config {
   static constexpr int MINB = (!FP64 && L == 3) ? 3 : 1;  // minimum resident CTAs per SM for the allocator
 };
 
+// The alternative FP32 launch shape of each lmax, the second candidate of
+// the autotuner (celes_ctx tuning): lmax 1-2 64-receiver CTAs, lmax 3 the
+// register allocator left free (two CTAs per SM), lmax 4 64-source tiles,
+// lmax 5 64-receiver CTAs.  Everything else as in Config.
+template <int L, typename R>
+struct ConfigAlt : Config<L, R> {
+  static constexpr int BLOCK = (L <= 2 || L == 5) ? 64 : 128;
+  static constexpr int TJ = L == 4 ? 64 : 32;
+  static constexpr int MINB = 1;
+};
+
 template <int L, typename R, typename C = Config<L, R>>
 struct Layout {
   static constexpr int NH = L * (L + 2);

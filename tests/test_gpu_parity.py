@@ -255,6 +255,50 @@ def test_preconditioner_apply_large_blocks(N, L, edge):
         B.celes_destroy(ctx)
 
 
+@pytest.mark.parametrize("N,L,poly,n", CLUSTERS)
+def test_coupling_alternative_fp32_shape(N, L, poly, n):
+    # the autotuner's second FP32 launch shape, forced, against the dense W
+    sc = synth.random_cluster(23, N + L, N, L, radius=100.0, fill=0.25, n=n, polydisperse=poly)
+    ctx = make_ctx(sc, variant=1)
+    try:
+        W = translation.coupling_matrix(sc.positions, sc.k, L)
+        x = synth.random_vector(23, 200 + N, (sc.N, sc.nmax))
+        y_ref = (W @ x.reshape(-1)).reshape(x.shape)
+        y = gpu_matvec(ctx, x, B.CELES_FP32)
+        if N == 1:
+            assert np.all(y == 0)
+        else:
+            assert rel(y, y_ref) < 1e-5
+        v, ch, _ = B.celes_coupling_shape(ctx, B.CELES_FP32)
+        assert v == 1 and ch >= 1
+    finally:
+        B.celes_destroy(ctx)
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_autotuner_picks_a_shape_and_keeps_the_result(L):
+    # the tuned context and an untuned one give the same product (to FP32
+    # rounding), and the tuned shape is reported
+    sc = synth.config2(0, N=1500, lmax=L)
+    x = synth.random_vector(24, L, (sc.N, sc.nmax))
+    c1 = make_ctx(sc)
+    c0 = make_ctx(sc, autotune=False)
+    try:
+        y1 = gpu_matvec(c1, x, B.CELES_FP32)
+        y0 = gpu_matvec(c0, x, B.CELES_FP32)
+        assert rel(y1, y0) < 1e-5
+        v, ch, ms = B.celes_coupling_shape(c1, B.CELES_FP32)
+        assert v in (0, 1) and ch >= 1 and ms > 0
+        v0, ch0, ms0 = B.celes_coupling_shape(c0, B.CELES_FP32)
+        assert v0 == 0 and ms0 == 0
+        rows = [0, 700, sc.N - 1]
+        ref = translation.coupling_matvec_rows(sc.positions, sc.k, L, x, rows)
+        assert rel(y1[rows], ref) < 1e-5
+    finally:
+        B.celes_destroy(c1)
+        B.celes_destroy(c0)
+
+
 def test_preconditioner_apply_and_preconditioned_solve():
     sc = synth.random_cluster(25, 0, 40, 2, radius=100.0, fill=0.3, n=1.6 + 0.01j)
     ctx = make_ctx(sc)
