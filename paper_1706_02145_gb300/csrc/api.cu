@@ -36,6 +36,7 @@ namespace celes {
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
                                        void* partial, double k, int chunks, cudaStream_t st);              \
   int coupling_rtr_rpb_##LL(int precision);                                                                \
+  int coupling_rtr_slices_##LL(int precision, int chunks);                                                 \
   int coupling_rtr_slots_##LL(int precision);                                                              \
   long long coupling_rtr_flops_##LL();                                                                     \
   int coupling_terms_export_##LL(int* idx, double* val, int cap);
@@ -43,6 +44,7 @@ namespace celes {
   cudaError_t launch_coupling_rtr_alt_##LL(int64_t N, const void* pos, const void* x, void* partial,       \
                                            double k, int chunks, cudaStream_t st);                         \
   int coupling_rtr_alt_rpb_##LL();                                                                         \
+  int coupling_rtr_alt_slices_##LL(int chunks);                                                            \
   int coupling_rtr_alt_slots_##LL();
 CELES_DECLARE_ALT(1)
 CELES_DECLARE_ALT(2)
@@ -105,6 +107,28 @@ int coupling_rtr_rpb_v(int L, int precision, int variant) {
     case 4: return coupling_rtr_alt_rpb_4();
     case 5: return coupling_rtr_alt_rpb_5();
     default: return 0;
+  }
+}
+// partial-sum slices a launch with `chunks` source chunks writes (the
+// cluster reduction of the shared-memory accumulator shapes divides it)
+int coupling_rtr_slices_v(int L, int precision, int variant, int chunks) {
+  if (variant == 0 || precision == CELES_FP64) {
+    switch (L) {
+      case 1: return coupling_rtr_slices_1(precision, chunks);
+      case 2: return coupling_rtr_slices_2(precision, chunks);
+      case 3: return coupling_rtr_slices_3(precision, chunks);
+      case 4: return coupling_rtr_slices_4(precision, chunks);
+      case 5: return coupling_rtr_slices_5(precision, chunks);
+      default: return chunks;
+    }
+  }
+  switch (L) {
+    case 1: return coupling_rtr_alt_slices_1(chunks);
+    case 2: return coupling_rtr_alt_slices_2(chunks);
+    case 3: return coupling_rtr_alt_slices_3(chunks);
+    case 4: return coupling_rtr_alt_slices_4(chunks);
+    case 5: return coupling_rtr_alt_slices_5(chunks);
+    default: return chunks;
   }
 }
 int coupling_rtr_slots_v(int L, int precision, int variant) {
@@ -341,7 +365,11 @@ int chunks_for(const celes_ctx* c, int64_t N, int precision, int variant, double
   const double target = waves * (slots > 0 ? slots : 2 * device_sms());
   int64_t ch = static_cast<int64_t>(std::ceil(target / static_cast<double>(rb)));
   ch = std::min<int64_t>(ch, std::max<int64_t>(1, N / 64));
-  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ch, 256)));
+  ch = std::max<int64_t>(1, std::min<int64_t>(ch, 256));
+  // a multiple of 8 (of 4 below 8): whole clusters for the partial-sum reduction
+  if (ch >= 8) ch = (ch + 7) / 8 * 8;
+  else if (ch >= 4) ch = 4;
+  return static_cast<int>(std::min<int64_t>(ch, 256));
 }
 
 int autotune(celes_ctx* c, int precision, const void* x, cudaStream_t st) {
@@ -440,6 +468,7 @@ int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision
   }
   const int variant = c->tune_variant[pi];
   const int chunks = c->tune_chunks[pi];
+  const int slices = use_rtr(c, precision) ? coupling_rtr_slices_v(c->L, precision, variant, chunks) : chunks;
   const size_t elem = precision == CELES_FP64 ? 16 : 8;
   const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
   CK(c->partial.ensure(per * chunks), "coupling scratch");
@@ -464,9 +493,9 @@ int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision
       if (s) return s;
     }
     if (precision == CELES_FP64)
-      CK(launch_coupling_epilogue<double>(c->N, c->L, chunks, c->partial.p, xr, c->tq.p, yr, mode, st), "epilogue");
+      CK(launch_coupling_epilogue<double>(c->N, c->L, slices, c->partial.p, xr, c->tq.p, yr, mode, st), "epilogue");
     else
-      CK(launch_coupling_epilogue<float>(c->N, c->L, chunks, c->partial.p, xr, c->tq32.p, yr, mode, st), "epilogue");
+      CK(launch_coupling_epilogue<float>(c->N, c->L, slices, c->partial.p, xr, c->tq32.p, yr, mode, st), "epilogue");
     if (c->profiling) {
       CK(cudaEventRecord(rec.b, st), "event");
       c->recs.push_back(rec);

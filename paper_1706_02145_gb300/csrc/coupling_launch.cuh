@@ -122,6 +122,9 @@ long long rtr_flops_per_pair_t() {
     return rtr::launch_partial<LL, float, rtr::ConfigAlt<LL, float>>(N, pos, x, partial, k, chunks, st);   \
   }                                                                                                         \
   int coupling_rtr_alt_rpb_##LL() { return rtr::ConfigAlt<LL, float>::BLOCK; }                             \
+  int coupling_rtr_alt_slices_##LL(int chunks) {                                                           \
+    return chunks / rtr::partial_cluster<LL, float, rtr::ConfigAlt<LL, float>>(chunks);                    \
+  }                                                                                                         \
   int coupling_rtr_alt_slots_##LL() { return rtr::resident_slots<LL, float, rtr::ConfigAlt<LL, float>>(); }
 
 #define CELES_INSTANTIATE_COUPLING(LL, FP64_UNROLLED)                                                       \
@@ -142,6 +145,10 @@ long long rtr_flops_per_pair_t() {
   }                                                                                                        \
   int coupling_rtr_rpb_##LL(int precision) {                                                               \
     return precision == 0 ? rtr::Config<LL, double>::BLOCK : rtr::Config<LL, float>::BLOCK;               \
+  }                                                                                                        \
+  int coupling_rtr_slices_##LL(int precision, int chunks) {                                                \
+    return chunks / (precision == 0 ? rtr::partial_cluster<LL, double>(chunks)                             \
+                                    : rtr::partial_cluster<LL, float>(chunks));                            \
   }                                                                                                        \
   int coupling_rpb_##LL(int precision) {                                                                   \
     if (precision == 0) return (FP64_UNROLLED) ? CouplingLayout<LL, double>::RPB : kGenericRPB;           \

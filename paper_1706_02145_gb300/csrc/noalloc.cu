@@ -24,6 +24,7 @@ namespace celes {
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
                                        void* partial, double k, int chunks, cudaStream_t st);              \
   int coupling_rtr_rpb_##LL(int precision);                                                                \
+  int coupling_rtr_slices_##LL(int precision, int chunks);                                                 \
   int coupling_rtr_slots_##LL(int precision);
 CELES_DECLARE_RTR(1)
 CELES_DECLARE_RTR(2)
@@ -88,6 +89,18 @@ int rtr_slots(int L, int precision) {
   }
 }
 
+int rtr_slices(int L, int precision, int chunks) {
+  using namespace celes;
+  switch (L) {
+    case 1: return coupling_rtr_slices_1(precision, chunks);
+    case 2: return coupling_rtr_slices_2(precision, chunks);
+    case 3: return coupling_rtr_slices_3(precision, chunks);
+    case 4: return coupling_rtr_slices_4(precision, chunks);
+    case 5: return coupling_rtr_slices_5(precision, chunks);
+    default: return chunks;
+  }
+}
+
 int rtr_rpb(int L, int precision) {
   using namespace celes;
   switch (L) {
@@ -131,10 +144,9 @@ extern "C" int celes_coupling_matvec_noalloc(int64_t N, int lmax, double k, cons
   const double k_bg = k;
   if (launch_rtr(lmax, precision, N, positions4, x, scratch, k_bg, static_cast<int>(chunks), st) != cudaSuccess)
     return CELES_ECUDA;
+  const int slices = rtr_slices(lmax, precision, static_cast<int>(chunks));
   const cudaError_t e = precision == CELES_FP64
-                            ? celes::launch_coupling_epilogue<double>(N, lmax, static_cast<int>(chunks), scratch, x,
-                                                                      nullptr, y, 0, st)
-                            : celes::launch_coupling_epilogue<float>(N, lmax, static_cast<int>(chunks), scratch, x,
-                                                                     nullptr, y, 0, st);
+                            ? celes::launch_coupling_epilogue<double>(N, lmax, slices, scratch, x, nullptr, y, 0, st)
+                            : celes::launch_coupling_epilogue<float>(N, lmax, slices, scratch, x, nullptr, y, 0, st);
   return e == cudaSuccess ? CELES_OK : CELES_ECUDA;
 }

@@ -14,6 +14,8 @@
 // O(L^3) work instead of the O(L^4) of the direct per-entry evaluation.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "coupling_kernel.cuh"
@@ -724,7 +726,11 @@ struct Layout {
 // One tile: receivers rb*BLOCK .. +BLOCK against sources j0 .. j1 - 1; writes
 // this tile's partial sums in the +- basis to out ([N][2][NH] complex, the
 // slice of the tile's source chunk).  Called by every thread of the CTA.
-template <int L, typename R, typename C>
+// CRED (shared-memory accumulators only): the CTAs of one thread-block
+// cluster (one receiver block, consecutive source chunks) add their sums
+// through distributed shared memory and write one partial per cluster, so
+// the partial-sum traffic shrinks by the cluster size.
+template <int L, typename R, typename C, bool CRED = false>
 __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
                                          Pair2<R>* __restrict__ outp, double k, int rb, int j0, int j1,
                                          unsigned char* smem_raw) {
@@ -815,6 +821,32 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
       }
     }
   }
+  if constexpr (CRED) {
+    static_assert(C::ACC_SMEM, "the cluster reduction reads shared-memory accumulators");
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncl = static_cast<int>(cl.num_blocks());
+    const int rk = static_cast<int>(cl.block_rank());
+    cl.sync();  // every CTA of the cluster has its sums in shared memory
+    if (active) {
+      Pair2<R>* out = outp + (size_t)i * (2 * NH);
+      // rows dealt round robin over the cluster's CTAs; ranks added in order
+      for (int r = rk; r < NH; r += ncl) {
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int q = 0; q < ncl; ++q) {
+          const Quad4<R> v = cl.map_shared_rank(sacc4, q)[r * BLOCK + tid];
+          a0 += v.x;
+          a1 += v.y;
+          a2 += v.z;
+          a3 += v.w;
+        }
+        out[r] = Pair2<R>{a0, a1};
+        out[NH + r] = Pair2<R>{a2, a3};
+      }
+    }
+    cl.sync();  // no CTA leaves while others read its shared memory
+    return;
+  }
   if (active) {
     // partial layout [2][NH] complex: y+ rows, then y- rows
     Pair2<R>* out = outp + (size_t)i * (2 * NH);
@@ -836,15 +868,18 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
 
 // grid (receiver blocks of BLOCK, source chunks); writes partial sums in the
 // +- basis, [chunks][N][2][NH] complex (same layout as the direct kernel)
-template <int L, typename R, typename C = Config<L, R>>
+// CRED: launched with clusters of `ncl` CTAs along y; cluster c writes
+// partial slice c (the grid's y extent is a multiple of ncl)
+template <int L, typename R, typename C = Config<L, R>, bool CRED = false>
 __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     rtr_partial_kernel(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
-                       Pair2<R>* __restrict__ partial, double k, int chunk) {
+                       Pair2<R>* __restrict__ partial, double k, int chunk, int ncl) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   constexpr int NH = L * (L + 2);
   const int j0 = blockIdx.y * chunk;
   const int j1 = min(N, j0 + chunk);
-  rtr_tile<L, R, C>(N, pos, x, partial + (size_t)blockIdx.y * N * (2 * NH), k, blockIdx.x, j0, j1, smem_raw);
+  const int slice = CRED ? static_cast<int>(blockIdx.y) / ncl : static_cast<int>(blockIdx.y);
+  rtr_tile<L, R, C, CRED>(N, pos, x, partial + (size_t)slice * N * (2 * NH), k, blockIdx.x, j0, j1, smem_raw);
 }
 
 // ---- batched form: one persistent launch over the tiles of many systems ----
@@ -915,7 +950,7 @@ template <int L, typename R, typename C = Config<L, R>>
 int partial_occupancy() {
   static PerDevice cache;
   return cache.get(current_device,
-                   [] { return kernel_setup(rtr_partial_kernel<L, R, C>, C::BLOCK, Layout<L, R, C>::bytes); });
+                   [] { return kernel_setup(rtr_partial_kernel<L, R, C, false>, C::BLOCK, Layout<L, R, C>::bytes); });
 }
 template <int L, typename R, typename C = Config<L, R>>
 int batch_occupancy() {
@@ -931,6 +966,33 @@ int resident_slots() {
   return device_sms() * (occ > 0 ? occ : 1);
 }
 
+// cluster size of the partial-sum reduction for `chunks` source chunks: the
+// largest of 8, 4, 2 that divides it (shared-memory accumulators only), else 1
+template <int L, typename R, typename C = Config<L, R>>
+int partial_cluster(int chunks) {
+  if constexpr (!C::ACC_SMEM) {
+    return 1;
+  } else {
+    for (int c = 8; c > 1; c >>= 1)
+      if (chunks % c == 0) return c;
+    return 1;
+  }
+}
+
+template <int L, typename R, typename C = Config<L, R>>
+int partial_cluster_occupancy() {
+  if constexpr (!C::ACC_SMEM) {
+    return 0;
+  } else {
+    static PerDevice cache;
+    return cache.get(current_device, [] {
+      return kernel_setup(rtr_partial_kernel<L, R, C, true>, C::BLOCK, Layout<L, R, C>::bytes);
+    });
+  }
+}
+
+// `chunks` source chunks; writes chunks / partial_cluster(chunks) partial
+// slices (the count the epilogue must add)
 template <int L, typename R, typename C = Config<L, R>>
 cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
                            cudaStream_t st) {
@@ -941,10 +1003,32 @@ cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* part
   if (chunks < 1) chunks = 1;
   const int64_t chunk = (N + chunks - 1) / chunks;
   dim3 grid(static_cast<unsigned>((N + C::BLOCK - 1) / C::BLOCK), static_cast<unsigned>(chunks));
-  rtr_partial_kernel<L, R, C><<<grid, C::BLOCK, LY::bytes, st>>>(static_cast<int>(N), static_cast<const Pos4*>(pos),
-                                                               static_cast<const Pair2<R>*>(x),
-                                                               static_cast<Pair2<R>*>(partial), k,
-                                                               static_cast<int>(chunk));
+  const int ncl = partial_cluster<L, R, C>(chunks);
+  if constexpr (C::ACC_SMEM) {
+    if (ncl > 1) {
+      if (partial_cluster_occupancy<L, R, C>() < 1) return cudaErrorInvalidConfiguration;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3(C::BLOCK);
+      cfg.dynamicSmemBytes = LY::bytes;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = static_cast<unsigned>(ncl);
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, rtr_partial_kernel<L, R, C, true>, static_cast<int>(N),
+                                               static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
+                                               static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk), ncl);
+      note_launch();
+      return e;
+    }
+  }
+  rtr_partial_kernel<L, R, C, false><<<grid, C::BLOCK, LY::bytes, st>>>(
+      static_cast<int>(N), static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
+      static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk), 1);
   note_launch();
   return cudaGetLastError();
 }
