@@ -91,6 +91,8 @@ def parse():
                     help="--case: slab = the bench recipe with --N spheres and --lmax; large = the 100 000-sphere "
                          "monodisperse slab (lmax 3)")
     ap.add_argument("--edge", type=float, default=900.0, help="--case precond: cuboid edge (nm)")
+    ap.add_argument("--autotune", type=int, default=1, help="--case coupling: 1 = tune the launch shape, 0 = built-in")
+    ap.add_argument("--variant", type=int, default=-1, help="--case coupling: force the FP32 launch shape (0 or 1)")
     ap.add_argument("--ensembles", type=int, default=12, help="--case batch: ensembles")
     ap.add_argument("--rhs", type=int, default=0,
                     help="--case: right-hand sides (0 = 1 for coupling, 4 plane waves per ensemble for batch)")
@@ -732,6 +734,12 @@ def run_ours(args, rank, world, local_rank):
     for key, pk in (("coupling_fp32", peaks["fp32_tflops"]), ("coupling_fp64", peaks["fp64_tflops"])):
         tf = kernels[key]["tflops"]
         kernels[key]["frac_of_measured_peak"] = (tf / pk) if tf else None
+    for key, prec in (("coupling_fp32", B.CELES_FP32), ("coupling_fp64", B.CELES_FP64)):
+        try:
+            v, ch, tms = B.celes_coupling_shape(ctx, prec)
+            kernels[key]["shape"] = {"variant": v, "chunks": ch, "tuned_ms": tms}
+        except B.CelesError:
+            pass
     dom = "coupling_fp32" if k32_ms >= k64_ms else "coupling_fp64"
     peak = peaks["fp32_tflops"] if dom == "coupling_fp32" else peaks["fp64_tflops"]
     ach = kernels[dom]["tflops"]
@@ -958,7 +966,8 @@ def run_case(args):
         return
     kern = {"auto": B.CELES_KERNEL_AUTO, "direct": B.CELES_KERNEL_DIRECT, "rtr": B.CELES_KERNEL_RTR}[args.kernel]
     sc = synth.config2(0, N=args.N, lmax=args.lmax) if args.recipe == "slab" else synth.config5(0)
-    ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, kernel=kern)
+    ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, kernel=kern,
+                         autotune=bool(args.autotune), variant=args.variant)
     nrhs = max(1, args.rhs) if args.case == "coupling" else 1
     x = torch.randn(nrhs, sc.N, sc.nmax, dtype=dt, device="cuda", generator=g)
     y = torch.empty_like(x)
@@ -981,8 +990,9 @@ def run_case(args):
               f"{nb} blocks, largest {maxd}): {t * 1e3:.3f} ms, factors {fb / 1e9:.3f} GB, {fb / t / 1e9:.1f} GB/s")
     else:
         pairs = sc.N * (sc.N - 1) * nrhs
+        shape = B.celes_coupling_shape(ctx, prec) if args.kernel != "direct" else None
         print(f"N={sc.N} lmax={sc.lmax} {args.precision} kernel={args.kernel} rhs={nrhs}: {t * 1e3:.3f} ms, "
-              f"{pairs / t:.3e} couplings/s")
+              f"{pairs / t:.3e} couplings/s, shape (variant, chunks, tuned ms) {shape}")
     B.celes_destroy(ctx)
 
 
