@@ -329,27 +329,7 @@ cudaError_t launch_precond_tile_inverse(int64_t nblocks, int64_t max_tiles, cons
 constexpr int kApplyThreads = 256;
 constexpr int kApplyClusterMaxSmem = 160 * 1024;  // largest block vector of the cluster form
 
-// split cluster barrier: arrive (release: this thread's earlier shared and
-// distributed-shared writes become visible to the cluster) and wait (acquire)
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
-
-// Tiles are dealt round robin: tile t belongs to the CTA of cluster rank
-// t mod C.  The two sweeps are one sequence of 2 ntile phases; phase p solves
-// tile p (forward, L) or 2 ntile - 1 - p (backward, U).  Its owner multiplies
-// the tile's rows by the explicit inverse of the diagonal tile, writes the 32
-// values into every CTA's copy of the block vector and arrives at the
-// cluster barrier; every other CTA arrived early and only waits.  While
-// waiting for phase p, the owner of phase p + 1 already stages that phase's
-// tile inverse and the 32 x 32 block of the factor that couples the two tiles
-// (neither depends on the vector), so its serial path after the barrier is
-// two small products from shared memory.  The rest of a CTA's rows take the
-// new column only after its own broadcast; since ownership rotates, that bulk
-// work overlaps the next C - 1 phases of the other CTAs.  Updates to a row
-// commute, so only the rows of a tile about to be solved must have every
-// earlier column applied.
+// FP64 vectors: the CTA of cluster rank s owns tiles [s * per, min(ntile, (s + 1) * per))
 template <typename R, typename F>
 __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
     const int64_t* __restrict__ block_off, const int64_t* __restrict__ mat_off, const int64_t* __restrict__ tile_off,
@@ -364,151 +344,292 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
   const int64_t s0 = block_off[q];
   const int64_t n = (block_off[q + 1] - s0) * nmax;
   const int64_t ntile = (n + 31) / 32;
+  const int64_t per = (ntile + C - 1) / C;
+  const int64_t t_lo = s * per < ntile ? s * per : ntile;
+  const int64_t t_hi = (s + 1) * per < ntile ? (s + 1) * per : ntile;
+  const int64_t r_lo = t_lo * 32, r_hi = t_hi * 32 < n ? t_hi * 32 : n;
   const Pair2<F>* A = mats + mat_off[q];
   const Pair2<F>* TI = tinv + tile_off[q];
   const int* pp = pivperm + s0 * nmax;
   const Pair2<R>* xr = x + (int64_t)rhs * N * nmax;
   Pair2<R>* yr = y + (int64_t)rhs * N * nmax;
   Pair2<F>* v = reinterpret_cast<Pair2<F>*>(pc_smem);  // [n]: own rows (partial sums) + solved tiles
-  __shared__ Pair2<F> dt[32][33];  // inverse of the next diagonal tile, dt[col][row]
-  __shared__ Pair2<F> ls[32][33];  // factor block coupling the next tile to the current one, ls[col][row]
+  __shared__ Pair2<F> dt[32][33];
   __shared__ Pair2<F> w[32];
-  __shared__ Pair2<F> red[kApplyThreads / 32][32];
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  constexpr int NW = kApplyThreads / 32;
-  const int64_t nphase = 2 * ntile;
-  auto tile_of = [&](int64_t p) { return p < ntile ? p : nphase - 1 - p; };
-  auto owns = [&](int64_t p) { return p >= 0 && p < nphase && (tile_of(p) % C) == s; };
-  auto tb_of = [&](int64_t t) { return static_cast<int>(n - t * 32 < 32 ? n - t * 32 : 32); };
-  // stage phase p's tile inverse and, when phase p - 1 is of the same sweep,
-  // the factor block A[tile(p) rows, tile(p - 1) columns]
-  auto prefetch = [&](int64_t p) {
-    const int64_t t = tile_of(p);
-    const Pair2<F>* Ti = TI + t * 2048 + (p < ntile ? 0 : 1024);
-    for (int e = tid; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
-    const bool same = p > 0 && ((p < ntile) == (p - 1 < ntile));
-    if (same) {
-      const int64_t rb = t * 32, cb = tile_of(p - 1) * 32;
-      const int tbr = tb_of(t), tbc = tb_of(tile_of(p - 1));
-      for (int e = tid; e < 1024; e += blockDim.x) {
-        const int c = e >> 5, r = e & 31;
-        ls[c][r] = (r < tbr && c < tbc) ? A[(rb + r) + (cb + c) * n] : Pair2<F>{0, 0};
-      }
-    }
-  };
-  // own rows of tiles beyond phase p's tile (in its sweep), except tile `skip`,
-  // updated with the column of phase p; one warp per tile, one lane per row
-  auto bulk_update = [&](int64_t p, int64_t skip) {
-    const int64_t kt = tile_of(p);
-    const int64_t kb = kt * 32;
-    const int tb = tb_of(kt);
-    const bool fwd = p < ntile;
-    // owned tiles after kt (fwd) or before kt (back), in order of distance
-    const int64_t first = fwd ? kt + 1 + ((s - (kt + 1) % C) % C + C) % C : kt - 1 - (((kt - 1) % C - s) % C + C) % C;
-    for (int64_t j = wid;; j += NW) {
-      const int64_t t = fwd ? first + j * C : first - j * C;
-      if (fwd ? t >= ntile : t < 0) break;
-      if (t == skip) continue;
-      if (lane < tb_of(t)) {
-        const int64_t i = t * 32 + lane;
-        v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
-      }
-    }
-  };
-
   // gather own rows (the pivot permutation folded in)
-  for (int64_t t0 = s; t0 < ntile; t0 += C) {
-    for (int r = tid; r < tb_of(t0); r += blockDim.x) {
-      const int64_t t = t0 * 32 + r;
-      const int64_t src = pp[t];
-      const int64_t a = src / nmax;
-      const int rr = static_cast<int>(src - a * nmax);
-      const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + rr];
-      v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
-    }
+  for (int64_t t = r_lo + threadIdx.x; t < r_hi; t += blockDim.x) {
+    const int64_t src = pp[t];
+    const int64_t a = src / nmax;
+    const int r = static_cast<int>(src - a * nmax);
+    const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
+    v[t] = Pair2<F>{static_cast<F>(e.re), static_cast<F>(e.im)};
   }
-  if (owns(0)) prefetch(0);
   __syncthreads();
-  if (!owns(0)) cluster_arrive();
-  int64_t pending = -1, pending_skip = -1;
-  for (int64_t p = 0; p < nphase; ++p) {
-    if (owns(p)) {
-      // rows of the tile: every earlier column applied; dt holds the inverse
-      const int64_t kb = tile_of(p) * 32;
-      const int tb = tb_of(tile_of(p));
-      if (tid < 32) {
-        F re = 0, im = 0;
-#pragma unroll 8
-        for (int c = 0; c < 32; ++c) {
-          if (c < tb) {
-            const Pair2<F> a = dt[c][lane], u = v[kb + c];
-            re += a.re * u.re - a.im * u.im;
-            im += a.re * u.im + a.im * u.re;
-          }
-        }
-        w[lane] = Pair2<F>{re, im};
-      }
-      __syncthreads();
-      for (int e = tid; e < C * 32; e += blockDim.x) {
-        const int dst = e >> 5, r = e & 31;
-        if (r < tb) cluster.map_shared_rank(v, dst)[kb + r] = w[r];
-      }
-      cluster_arrive();
-      if (pending >= 0) {
-        bulk_update(pending, pending_skip);
-        pending = -1;
-      }
-    }
-    const bool next = owns(p + 1);
-    if (next) prefetch(p + 1);  // independent of the vector: overlaps the wait
-    cluster_wait();             // phase p complete: its tile's values are in v
-    __syncthreads();
-    if (next) {
-      const bool same = (p + 1 < ntile) || (p >= ntile);
-      if (same) {
-        // rows of tile(p + 1) -= ls * v[tile(p)], columns split over the warps
-        const int64_t rb = tile_of(p + 1) * 32, cb = tile_of(p) * 32;
-        F re = 0, im = 0;
-        for (int c = wid; c < 32; c += NW) {
-          const Pair2<F> a = ls[c][lane], u = v[cb + (c < tb_of(tile_of(p)) ? c : 0)];
-          if (c < tb_of(tile_of(p))) {
-            re += a.re * u.re - a.im * u.im;
-            im += a.re * u.im + a.im * u.re;
-          }
-        }
-        red[wid][lane] = Pair2<F>{re, im};
+  const int lane = threadIdx.x & 31;
+  // one triangular sweep; fwd: tiles 0..ntile-1 with L, else ntile-1..0 with U
+  auto sweep = [&](bool fwd) {
+    for (int64_t step = 0; step < ntile; ++step) {
+      const int64_t k = fwd ? step : ntile - 1 - step;
+      const int64_t kb = k * 32;
+      const int tb = static_cast<int>(n - kb < 32 ? n - kb : 32);
+      const bool owner = k >= t_lo && k < t_hi;
+      if (owner) {
+        const Pair2<F>* Ti = TI + k * 2048 + (fwd ? 0 : 1024);
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) dt[e >> 5][e & 31] = Ti[e];
         __syncthreads();
-        if (tid < 32 && lane < tb_of(tile_of(p + 1))) {
-          Pair2<F> acc = v[rb + lane];
-#pragma unroll
-          for (int g = 0; g < NW; ++g) {
-            acc.re -= red[g][lane].re;
-            acc.im -= red[g][lane].im;
+        if (threadIdx.x < 32) {
+          F re = 0, im = 0;
+#pragma unroll 8
+          for (int c = 0; c < 32; ++c) {
+            if (c < tb) {
+              const Pair2<F> a = dt[c][lane], u = v[kb + c];
+              re += a.re * u.re - a.im * u.im;
+              im += a.re * u.im + a.im * u.re;
+            }
           }
-          v[rb + lane] = acc;
+          w[lane] = Pair2<F>{re, im};
+        }
+        __syncthreads();
+        // the solved tile into every CTA's copy of the block vector
+        for (int e = threadIdx.x; e < C * 32; e += blockDim.x) {
+          const int dst = e >> 5, r = e & 31;
+          if (r < tb) cluster.map_shared_rank(v, dst)[kb + r] = w[r];
         }
       }
-      __syncthreads();
-      pending = p;
-      pending_skip = tile_of(p + 1);
-    } else {
-      if (p + 1 < nphase) cluster_arrive();
-      bulk_update(p, -1);
+      cluster.sync();
+      // apply tile column k to own rows below (fwd) / above (back) the tile
+      const int64_t a0 = fwd ? (r_lo > kb + tb ? r_lo : kb + tb) : r_lo;
+      const int64_t a1 = fwd ? r_hi : (r_hi < kb ? r_hi : kb);
+      for (int64_t i = a0 + threadIdx.x; i < a1; i += blockDim.x) v[i] = tile_gemv(A, n, i, kb, tb, v, v[i]);
       __syncthreads();
     }
-  }
-  for (int64_t t0 = s; t0 < ntile; t0 += C) {
-    for (int r = tid; r < tb_of(t0); r += blockDim.x) {
-      const int64_t t = t0 * 32 + r;
-      const int64_t a = t / nmax;
-      const int rr = static_cast<int>(t - a * nmax);
-      yr[(int64_t)perm[s0 + a] * nmax + rr] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
-    }
+  };
+  sweep(true);
+  sweep(false);
+  for (int64_t t = r_lo + threadIdx.x; t < r_hi; t += blockDim.x) {
+    const int64_t a = t / nmax;
+    const int r = static_cast<int>(t - a * nmax);
+    yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(v[t].re), static_cast<R>(v[t].im)};
   }
   // no CTA leaves while others may still write its shared memory
-  cluster_arrive();
-  cluster_wait();
+  cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 vectors: the block solve as two triangular products with explicit
+// inverses.  At build time the FP32 copies of each block's factors are turned
+// into L^{-1} (strictly lower part; unit diagonal implied) and U^{-1} (upper
+// part with the diagonal), stored in the same n x n column-major slot.  The
+// apply x = U^{-1} (L^{-1} (P y)) is then two matrix-vector products with no
+// serial chain: a cluster of C CTAs per block deals the 32-row tiles round
+// robin, computes its rows of t = L^{-1} P y, writes them into every CTA's
+// copy of t, meets the others at one cluster barrier and computes its rows of
+// x = U^{-1} t.  It reads the same bytes as a substitution (one entry per
+// factor element) and is bound by memory bandwidth.  A preconditioner only
+// has to be a fixed linear operator close to the block inverse; the inverses
+// are formed from the FP32 rounding of the FP64 LU factors.
+// ---------------------------------------------------------------------------
+
+// Column tile j of L^{-1} (z = 0) or U^{-1} (z = 1) of block q, by blocked
+// substitution: X_jj = (tile inverse), and for the other row tiles i (below j
+// for L, above for U) X_ij = -inv(T_ii) sum_k T_ik X_kj over the tiles k
+// between them.  One CTA of 256 threads per (column tile, block, factor);
+// thread (row r, column group g) owns X[r][4g .. 4g + 3].
+__global__ void __launch_bounds__(256) precond_tri_inverse_kernel(const int64_t* __restrict__ block_off,
+                                                                  const int64_t* __restrict__ mat_off,
+                                                                  const int64_t* __restrict__ tile_off, int nmax,
+                                                                  const float2* __restrict__ lu,
+                                                                  const float2* __restrict__ tinv,
+                                                                  float2* __restrict__ inv) {
+  const int64_t q = blockIdx.y;
+  const int64_t n = (block_off[q + 1] - block_off[q]) * nmax;
+  const int64_t T = (n + 31) / 32;
+  const int64_t j = blockIdx.x;
+  if (j >= T) return;
+  const bool upper = blockIdx.z == 1;
+  const float2* A = lu + mat_off[q];
+  float2* X = inv + mat_off[q];
+  const float2* TI = tinv + tile_off[q];
+  __shared__ float2 as[32][33];  // as[m][r]: factor tile, column m, row r
+  __shared__ float2 xs[32][33];  // xs[c][m]: X tile, column c, row m
+  const int tid = threadIdx.x;
+  const int r = tid & 31, g = tid >> 5;
+  auto tb_of = [&](int64_t t) { return static_cast<int>(n - t * 32 < 32 ? n - t * 32 : 32); };
+  const int tbj = tb_of(j);
+  // stage tile (ti, tk) of a column-major n x n matrix as dst[col][row]
+  // (zero outside the block)
+  auto load_tile = [&](float2 (*dst)[33], const float2* M, int64_t ti, int64_t tk) {
+    const int tbr = tb_of(ti), tbc = tb_of(tk);
+    for (int e = tid; e < 1024; e += 256) {
+      const int c = e >> 5, rr = e & 31;
+      dst[c][rr] = (rr < tbr && c < tbc) ? M[(ti * 32 + rr) + (tk * 32 + c) * n] : make_float2(0.f, 0.f);
+    }
+  };
+  // the inverse of diagonal tile t (the whole unit-lower L or upper U
+  // inverse, identity-padded), as dst[col][row]
+  auto load_tinv = [&](float2 (*dst)[33], int64_t t) {
+    const float2* Ti = TI + t * 2048 + (upper ? 1024 : 0);
+    for (int e = tid; e < 1024; e += 256) dst[e >> 5][e & 31] = Ti[e];
+  };
+  // X_jj: write its part (strictly lower for L, upper for U) into the slot
+  load_tinv(xs, j);
+  __syncthreads();
+  for (int e = tid; e < 1024; e += 256) {
+    const int c = e >> 5, rr = e & 31;
+    if (rr < tbj && c < tbj && (upper ? rr <= c : rr > c)) X[(j * 32 + rr) + (j * 32 + c) * n] = xs[c][rr];
+  }
+  __syncthreads();
+  const int64_t i0 = upper ? j - 1 : j + 1;
+  const int64_t di = upper ? -1 : 1;
+  for (int64_t i = i0; upper ? i >= 0 : i < T; i += di) {
+    float2 acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+    // S = sum over the tiles k strictly between i and j, and k = j
+    const int64_t k0 = upper ? i + 1 : j, k1 = upper ? j : i - 1;
+    for (int64_t k = k0; k <= k1; ++k) {
+      load_tile(as, A, i, k);  // as[m][r] = T_ik[r][m]
+      if (k == j) load_tinv(xs, j);
+      else load_tile(xs, X, k, j);  // xs[c][m] = X_kj[m][c]
+      __syncthreads();
+#pragma unroll 8
+      for (int m = 0; m < 32; ++m) {
+        const float2 a = as[m][r];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 b = xs[4 * g + u][m];
+          acc[u].x += a.x * b.x - a.y * b.y;
+          acc[u].y += a.x * b.y + a.y * b.x;
+        }
+      }
+      __syncthreads();
+    }
+    // X_ij = -inv(T_ii) S
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xs[4 * g + u][r] = acc[u];
+    load_tinv(as, i);
+    __syncthreads();
+    float2 out[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[u] = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int m = 0; m < 32; ++m) {
+      const float2 a = as[m][r];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 b = xs[4 * g + u][m];
+        out[u].x -= a.x * b.x - a.y * b.y;
+        out[u].y -= a.x * b.y + a.y * b.x;
+      }
+    }
+    const int tbi = tb_of(i);
+    if (r < tbi) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = 4 * g + u;
+        if (c < tbj) X[(i * 32 + r) + (j * 32 + c) * n] = out[u];
+      }
+    }
+    __syncthreads();  // X_ij is read back by the next row tiles
+  }
+}
+constexpr int kInvThreads = 256;
+
+// x = U^{-1} (L^{-1} (P y)) for one (block, RHS) per cluster of C CTAs; the
+// 32-row tiles are dealt round robin (warp w of CTA s takes tiles s + C (w +
+// 8 m)), one lane per row, so each column of a tile is one coalesced 256-byte
+// read.  Every CTA gathers the whole (pivot-permuted) block vector.
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const int64_t* __restrict__ block_off,
+                                                                        const int64_t* __restrict__ mat_off, int nmax,
+                                                                        const int* __restrict__ perm,
+                                                                        const float2* __restrict__ inv,
+                                                                        const int* __restrict__ pivperm, int64_t N,
+                                                                        const Pair2<R>* __restrict__ x,
+                                                                        Pair2<R>* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char pi_smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = static_cast<int>(cluster.num_blocks());
+  const int s = static_cast<int>(cluster.block_rank());
+  const int64_t q = blockIdx.x / C;
+  const int rhs = blockIdx.y;
+  const int64_t s0 = block_off[q];
+  const int64_t n = (block_off[q + 1] - s0) * nmax;
+  const int64_t T = (n + 31) / 32;
+  const float2* A = inv + mat_off[q];
+  const int* pp = pivperm + s0 * nmax;
+  const Pair2<R>* xr = x + (int64_t)rhs * N * nmax;
+  Pair2<R>* yr = y + (int64_t)rhs * N * nmax;
+  float2* xv = reinterpret_cast<float2*>(pi_smem);  // [n] P y
+  float2* tv = xv + n;                              // [n] t = L^{-1} P y
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = kInvThreads / 32;
+  for (int64_t t = tid; t < n; t += blockDim.x) {
+    const int64_t src = pp[t];
+    const int64_t a = src / nmax;
+    const int r = static_cast<int>(src - a * nmax);
+    const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
+    xv[t] = make_float2(static_cast<float>(e.re), static_cast<float>(e.im));
+  }
+  __syncthreads();
+  // row i of a lower (upper) product: sum over columns [j0, j1) of A[i, j] v[j]
+  auto rowdot = [&](int64_t i, int64_t j0, int64_t j1, const float2* v) {
+    float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
+    const float2* a = A + i;
+    int64_t jj = j0;
+    for (; jj + 8 <= j1; jj += 8) {
+      float2 m[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) m[u] = a[(jj + u) * n];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const float2 v0 = v[jj + u], v1 = v[jj + u + 1];
+        ar0 += m[u].x * v0.x - m[u].y * v0.y;
+        ai0 += m[u].x * v0.y + m[u].y * v0.x;
+        ar1 += m[u + 1].x * v1.x - m[u + 1].y * v1.y;
+        ai1 += m[u + 1].x * v1.y + m[u + 1].y * v1.x;
+      }
+    }
+    for (; jj < j1; ++jj) {
+      const float2 m = a[jj * n], v0 = v[jj];
+      ar0 += m.x * v0.x - m.y * v0.y;
+      ai0 += m.x * v0.y + m.y * v0.x;
+    }
+    return make_float2(ar0 + ar1, ai0 + ai1);
+  };
+  // t = L^{-1} P y on own tiles (unit diagonal), into every CTA's copy of t
+  for (int64_t tt = s + (int64_t)C * wid; tt < T; tt += (int64_t)C * NW) {
+    const int64_t i = tt * 32 + lane;
+    if (i < n) {
+      const float2 d = rowdot(i, 0, i, xv);
+      const float2 t = make_float2(xv[i].x + d.x, xv[i].y + d.y);
+      for (int dst = 0; dst < C; ++dst) cluster.map_shared_rank(tv, dst)[i] = t;
+    }
+  }
+  cluster.sync();
+  // x = U^{-1} t on own tiles
+  for (int64_t tt = s + (int64_t)C * wid; tt < T; tt += (int64_t)C * NW) {
+    const int64_t i = tt * 32 + lane;
+    if (i < n) {
+      const float2 o = rowdot(i, i, n, tv);
+      const int64_t a = i / nmax;
+      const int r = static_cast<int>(i - a * nmax);
+      yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(o.x), static_cast<R>(o.y)};
+    }
+  }
+}
+
+cudaError_t launch_precond_tri_inverse(int64_t nblocks, int64_t max_tiles, const int64_t* block_off,
+                                       const int64_t* mat_off, const int64_t* tile_off, int nmax, const float* lu32,
+                                       const float* tinv32, float* inv32, cudaStream_t st) {
+  if (nblocks <= 0 || max_tiles <= 0) return cudaSuccess;
+  dim3 grid(static_cast<unsigned>(max_tiles), static_cast<unsigned>(nblocks), 2);
+  precond_tri_inverse_kernel<<<grid, 256, 0, st>>>(block_off, mat_off, tile_off, nmax,
+                                                   reinterpret_cast<const float2*>(lu32),
+                                                   reinterpret_cast<const float2*>(tinv32),
+                                                   reinterpret_cast<float2*>(inv32));
+  note_launch();
+  return cudaGetLastError();
 }
 
 // position -> source index of the row interchanges of each block's LU
@@ -610,16 +731,60 @@ int precond_cluster_size(double mean_tiles) {
   return 1;
 }
 
-// FP64 vectors use the FP64 factors; FP32 vectors the FP32 copy (mats32).
-// With tile inverses (tinv non-null) and a block vector that fits in shared
-// memory, the cluster form runs; otherwise the one-CTA-per-block form.
+// the FP32 inverse form fits when both block vectors fit in shared memory
+bool precond_inverse_fits(int max_block_dim) {
+  return 2 * sizeof(float2) * static_cast<size_t>(max_block_dim) <= kApplyClusterMaxSmem;
+}
+
+cudaError_t launch_apply_inv(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
+                             const int* perm, const float* inv32, const int* pivperm, int64_t N, int nrhs,
+                             const void* x, void* y, int max_block_dim, int csize, cudaStream_t st) {
+  static PerDevice attr;
+  cudaError_t se = cudaSuccess;
+  if (attr.get(current_device, [&] {
+        se = cudaFuncSetAttribute(precond_apply_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kApplyClusterMaxSmem);
+        return se == cudaSuccess ? 1 : 0;
+      }) == 0)
+    return se != cudaSuccess ? se : cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(nblocks * csize), static_cast<unsigned>(nrhs));
+  cfg.blockDim = dim3(kInvThreads);
+  cfg.dynamicSmemBytes = 2 * sizeof(float2) * static_cast<size_t>(max_block_dim);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(csize);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, precond_apply_inv_kernel<float>, block_off, mat_off, nmax, perm,
+                                           reinterpret_cast<const float2*>(inv32), pivperm, N,
+                                           static_cast<const Pair2<float>*>(x), static_cast<Pair2<float>*>(y));
+  note_launch();
+  return e;
+}
+
+// FP64 vectors use the FP64 factors; FP32 vectors the FP32 copy (mats32),
+// which holds the explicit inverses of L and U when fp32_inverse is set
+// (the two-product form), else the FP32 LU factors.  With tile inverses
+// (tinv non-null) and a block vector that fits in shared memory, the FP64
+// (and FP32 LU) solves run in the cluster substitution form; otherwise in the
+// one-CTA-per-block form.
 template <typename R>
 cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
                                  const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
                                  int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st,
-                                 const int64_t* tile_off, const double* tinv, const float* tinv32, int csize) {
+                                 const int64_t* tile_off, const double* tinv, const float* tinv32, int csize,
+                                 bool fp32_inverse) {
   if (nblocks <= 0) return cudaSuccess;
   constexpr size_t esz = sizeof(R) == 8 ? 16 : 8;
+  if constexpr (sizeof(R) == 4) {
+    if (fp32_inverse)
+      return launch_apply_inv(nblocks, block_off, mat_off, nmax, perm, mats32, piv, N, nrhs, x, y, max_block_dim,
+                              csize >= 1 ? csize : 1, st);
+  }
   if (tinv && csize >= 1 && esz * static_cast<size_t>(max_block_dim) <= kApplyClusterMaxSmem) {
     if constexpr (sizeof(R) == 8)
       return launch_apply_cluster_t<double, double>(nblocks, block_off, mat_off, tile_off, nmax, perm, mats, tinv,
@@ -638,11 +803,11 @@ cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, cons
 template cudaError_t launch_precond_apply<float>(int64_t, const int64_t*, const int64_t*, int, const int*,
                                                  const double*, const float*, const int*, int64_t, int, const void*,
                                                  void*, double*, int, cudaStream_t, const int64_t*, const double*,
-                                                 const float*, int);
+                                                 const float*, int, bool);
 template cudaError_t launch_precond_apply<double>(int64_t, const int64_t*, const int64_t*, int, const int*,
                                                   const double*, const float*, const int*, int64_t, int, const void*,
                                                   void*, double*, int, cudaStream_t, const int64_t*, const double*,
-                                                  const float*, int);
+                                                  const float*, int, bool);
 
 __global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
