@@ -254,7 +254,7 @@ struct celes_ctx {
   DevBuf block_off, mat_off, perm, mats, mats32, piv, pivperm, info, pwork;
   DevBuf tile_off, tinv, tinv32;  // explicit inverses of the diagonal 32 x 32 tiles of L and U
   int precond_csize = 1;          // CTAs per block in the cluster-form apply
-  bool precond_fp32_inverse = false;  // mats32 holds FP32 inverses of L and U (two-product apply)
+  bool precond_inverse = false;  // mats / mats32 hold the inverses of L and U (two-product apply)
   // small device scratch
   DevBuf dots, dot_partial, flag;
   std::string err;
@@ -888,19 +888,22 @@ extern "C" int celes_precond_build(celes_ctx* c, double edge) {
      "tile inverses");
   CK(launch_f64_to_f32(2 * toff[nb], c->tinv.as<double>(), c->tinv32.as<float>(), c->stream), "FP32 tile inverses");
   c->precond_csize = precond_cluster_size(static_cast<double>(toff[nb] / 2048) / static_cast<double>(nb));
-  // FP32 apply: replace the FP32 LU copy by the explicit inverses of L and U
-  c->precond_fp32_inverse = false;
+  // the apply's operator: the explicit inverses of L and U (FP64, and their
+  // FP32 rounding), in place of the LU factors, when the block vectors fit in
+  // shared memory
+  c->precond_inverse = false;
   if (precond_inverse_fits(static_cast<int>(max_dim))) {
     DevBuf inv;
-    CK(inv.ensure(sizeof(float) * 2 * moff[nb]), "FP32 inverse factors");
+    CK(inv.ensure(sizeof(double) * 2 * moff[nb]), "inverse factors");
     CK(launch_precond_tri_inverse(nb, max_tiles, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(),
-                                  c->tile_off.as<int64_t>(), c->nmax, c->mats32.as<float>(), c->tinv32.as<float>(),
-                                  inv.as<float>(), c->stream),
-       "FP32 inverse factors");
+                                  c->tile_off.as<int64_t>(), c->nmax, c->mats.as<double>(), c->tinv.as<double>(),
+                                  inv.as<double>(), c->stream),
+       "inverse factors");
     CK(cudaStreamSynchronize(c->stream), "sync");
-    std::swap(c->mats32.p, inv.p);
-    std::swap(c->mats32.bytes, inv.bytes);
-    c->precond_fp32_inverse = true;
+    std::swap(c->mats.p, inv.p);
+    std::swap(c->mats.bytes, inv.bytes);
+    CK(launch_f64_to_f32(2 * moff[nb], c->mats.as<double>(), c->mats32.as<float>(), c->stream), "FP32 inverses");
+    c->precond_inverse = true;
   }
   CK(c->pivperm.ensure(sizeof(int) * c->N * c->nmax), "pivot permutation");
   CK(launch_pivot_perm(nb, c->block_off.as<int64_t>(), c->nmax, c->piv.as<int>(), c->pivperm.as<int>(), c->stream),
@@ -943,14 +946,14 @@ static int precond_apply_internal(celes_ctx* c, const void* x, void* y, int nrhs
                                     c->perm.as<int>(), c->mats.as<double>(), c->mats32.as<float>(), c->pivperm.as<int>(),
                                     c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st,
                                     c->tile_off.as<int64_t>(), c->tinv.as<double>(), c->tinv32.as<float>(),
-                                    c->precond_csize, false),
+                                    c->precond_csize, c->precond_inverse),
        "precond apply");
   else
     CK(launch_precond_apply<float>(c->nblocks, c->block_off.as<int64_t>(), c->mat_off.as<int64_t>(), c->nmax,
                                    c->perm.as<int>(), c->mats.as<double>(), c->mats32.as<float>(), c->pivperm.as<int>(),
                                    c->N, nrhs, x, y, c->pwork.as<double>(), c->max_block_dim, st,
                                    c->tile_off.as<int64_t>(), c->tinv.as<double>(), c->tinv32.as<float>(),
-                                   c->precond_csize, c->precond_fp32_inverse),
+                                   c->precond_csize, c->precond_inverse),
        "precond apply");
   return CELES_OK;
 }

@@ -124,12 +124,12 @@ cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, cons
                                  const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
                                  int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st,
                                  const int64_t* tile_off = nullptr, const double* tinv = nullptr,
-                                 const float* tinv32 = nullptr, int csize = 0, bool fp32_inverse = false);
-// FP32 explicit inverses of each block's L and U from its FP32 LU factors and
-// FP32 tile inverses (same layout as the factors); used by the FP32 apply
+                                 const float* tinv32 = nullptr, int csize = 0, bool inverse = false);
+// FP64 explicit inverses of each block's L and U from its FP64 LU factors and
+// FP64 tile inverses (same layout as the factors)
 cudaError_t launch_precond_tri_inverse(int64_t nblocks, int64_t max_tiles, const int64_t* block_off,
-                                       const int64_t* mat_off, const int64_t* tile_off, int nmax, const float* lu32,
-                                       const float* tinv32, float* inv32, cudaStream_t st);
+                                       const int64_t* mat_off, const int64_t* tile_off, int nmax, const double* lu,
+                                       const double* tinv, double* inv, cudaStream_t st);
 bool precond_inverse_fits(int max_block_dim);
 cudaError_t launch_precond_tile_inverse(int64_t nblocks, int64_t max_tiles, const int64_t* block_off,
                                         const int64_t* mat_off, const int64_t* tile_off, int nmax, const double* mats,

@@ -416,18 +416,19 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// FP32 vectors: the block solve as two triangular products with explicit
-// inverses.  At build time the FP32 copies of each block's factors are turned
-// into L^{-1} (strictly lower part; unit diagonal implied) and U^{-1} (upper
-// part with the diagonal), stored in the same n x n column-major slot.  The
+// The block solve as two triangular products with explicit inverses.  At
+// build time each block's FP64 factors are turned into L^{-1} (strictly lower
+// part; unit diagonal implied) and U^{-1} (upper part with the diagonal), in
+// FP64, stored in the same n x n column-major slot (an FP32 copy serves FP32
+// vectors).  The
 // apply x = U^{-1} (L^{-1} (P y)) is then two matrix-vector products with no
 // serial chain: a cluster of C CTAs per block deals the 32-row tiles round
 // robin, computes its rows of t = L^{-1} P y, writes them into every CTA's
 // copy of t, meets the others at one cluster barrier and computes its rows of
 // x = U^{-1} t.  It reads the same bytes as a substitution (one entry per
 // factor element) and is bound by memory bandwidth.  A preconditioner only
-// has to be a fixed linear operator close to the block inverse; the inverses
-// are formed from the FP32 rounding of the FP64 LU factors.
+// has to be a fixed linear operator close to the block inverse; forming the
+// inverses in FP64 keeps the FP32 copy within FP32 rounding of the FP64 one.
 // ---------------------------------------------------------------------------
 
 // Column tile j of L^{-1} (z = 0) or U^{-1} (z = 1) of block q, by blocked
@@ -435,40 +436,42 @@ __global__ void __launch_bounds__(kApplyThreads) precond_apply_cluster_kernel(
 // for L, above for U) X_ij = -inv(T_ii) sum_k T_ik X_kj over the tiles k
 // between them.  One CTA of 256 threads per (column tile, block, factor);
 // thread (row r, column group g) owns X[r][4g .. 4g + 3].
+template <typename F>
 __global__ void __launch_bounds__(256) precond_tri_inverse_kernel(const int64_t* __restrict__ block_off,
                                                                   const int64_t* __restrict__ mat_off,
                                                                   const int64_t* __restrict__ tile_off, int nmax,
-                                                                  const float2* __restrict__ lu,
-                                                                  const float2* __restrict__ tinv,
-                                                                  float2* __restrict__ inv) {
+                                                                  const Pair2<F>* __restrict__ lu,
+                                                                  const Pair2<F>* __restrict__ tinv,
+                                                                  Pair2<F>* __restrict__ inv) {
+  using V = Pair2<F>;
   const int64_t q = blockIdx.y;
   const int64_t n = (block_off[q + 1] - block_off[q]) * nmax;
   const int64_t T = (n + 31) / 32;
   const int64_t j = blockIdx.x;
   if (j >= T) return;
   const bool upper = blockIdx.z == 1;
-  const float2* A = lu + mat_off[q];
-  float2* X = inv + mat_off[q];
-  const float2* TI = tinv + tile_off[q];
-  __shared__ float2 as[32][33];  // as[m][r]: factor tile, column m, row r
-  __shared__ float2 xs[32][33];  // xs[c][m]: X tile, column c, row m
+  const V* A = lu + mat_off[q];
+  V* X = inv + mat_off[q];
+  const V* TI = tinv + tile_off[q];
+  __shared__ V as[32][33];  // as[m][r]: factor tile, column m, row r
+  __shared__ V xs[32][33];  // xs[c][m]: X tile, column c, row m
   const int tid = threadIdx.x;
   const int r = tid & 31, g = tid >> 5;
   auto tb_of = [&](int64_t t) { return static_cast<int>(n - t * 32 < 32 ? n - t * 32 : 32); };
   const int tbj = tb_of(j);
   // stage tile (ti, tk) of a column-major n x n matrix as dst[col][row]
   // (zero outside the block)
-  auto load_tile = [&](float2 (*dst)[33], const float2* M, int64_t ti, int64_t tk) {
+  auto load_tile = [&](V (*dst)[33], const V* M, int64_t ti, int64_t tk) {
     const int tbr = tb_of(ti), tbc = tb_of(tk);
     for (int e = tid; e < 1024; e += 256) {
       const int c = e >> 5, rr = e & 31;
-      dst[c][rr] = (rr < tbr && c < tbc) ? M[(ti * 32 + rr) + (tk * 32 + c) * n] : make_float2(0.f, 0.f);
+      dst[c][rr] = (rr < tbr && c < tbc) ? M[(ti * 32 + rr) + (tk * 32 + c) * n] : V{0, 0};
     }
   };
   // the inverse of diagonal tile t (the whole unit-lower L or upper U
   // inverse, identity-padded), as dst[col][row]
-  auto load_tinv = [&](float2 (*dst)[33], int64_t t) {
-    const float2* Ti = TI + t * 2048 + (upper ? 1024 : 0);
+  auto load_tinv = [&](V (*dst)[33], int64_t t) {
+    const V* Ti = TI + t * 2048 + (upper ? 1024 : 0);
     for (int e = tid; e < 1024; e += 256) dst[e >> 5][e & 31] = Ti[e];
   };
   // X_jj: write its part (strictly lower for L, upper for U) into the slot
@@ -482,9 +485,9 @@ __global__ void __launch_bounds__(256) precond_tri_inverse_kernel(const int64_t*
   const int64_t i0 = upper ? j - 1 : j + 1;
   const int64_t di = upper ? -1 : 1;
   for (int64_t i = i0; upper ? i >= 0 : i < T; i += di) {
-    float2 acc[4];
+    V acc[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int u = 0; u < 4; ++u) acc[u] = V{0, 0};
     // S = sum over the tiles k strictly between i and j, and k = j
     const int64_t k0 = upper ? i + 1 : j, k1 = upper ? j : i - 1;
     for (int64_t k = k0; k <= k1; ++k) {
@@ -494,12 +497,12 @@ __global__ void __launch_bounds__(256) precond_tri_inverse_kernel(const int64_t*
       __syncthreads();
 #pragma unroll 8
       for (int m = 0; m < 32; ++m) {
-        const float2 a = as[m][r];
+        const V a = as[m][r];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 b = xs[4 * g + u][m];
-          acc[u].x += a.x * b.x - a.y * b.y;
-          acc[u].y += a.x * b.y + a.y * b.x;
+          const V b = xs[4 * g + u][m];
+          acc[u].re += a.re * b.re - a.im * b.im;
+          acc[u].im += a.re * b.im + a.im * b.re;
         }
       }
       __syncthreads();
@@ -509,17 +512,17 @@ __global__ void __launch_bounds__(256) precond_tri_inverse_kernel(const int64_t*
     for (int u = 0; u < 4; ++u) xs[4 * g + u][r] = acc[u];
     load_tinv(as, i);
     __syncthreads();
-    float2 out[4];
+    V out[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) out[u] = make_float2(0.f, 0.f);
+    for (int u = 0; u < 4; ++u) out[u] = V{0, 0};
 #pragma unroll 8
     for (int m = 0; m < 32; ++m) {
-      const float2 a = as[m][r];
+      const V a = as[m][r];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float2 b = xs[4 * g + u][m];
-        out[u].x -= a.x * b.x - a.y * b.y;
-        out[u].y -= a.x * b.y + a.y * b.x;
+        const V b = xs[4 * g + u][m];
+        out[u].re -= a.re * b.re - a.im * b.im;
+        out[u].im -= a.re * b.im + a.im * b.re;
       }
     }
     const int tbi = tb_of(i);
@@ -539,14 +542,15 @@ constexpr int kInvThreads = 256;
 // 32-row tiles are dealt round robin (warp w of CTA s takes tiles s + C (w +
 // 8 m)), one lane per row, so each column of a tile is one coalesced 256-byte
 // read.  Every CTA gathers the whole (pivot-permuted) block vector.
-template <typename R>
+template <typename R, typename F>
 __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const int64_t* __restrict__ block_off,
                                                                         const int64_t* __restrict__ mat_off, int nmax,
                                                                         const int* __restrict__ perm,
-                                                                        const float2* __restrict__ inv,
+                                                                        const Pair2<F>* __restrict__ inv,
                                                                         const int* __restrict__ pivperm, int64_t N,
                                                                         const Pair2<R>* __restrict__ x,
                                                                         Pair2<R>* __restrict__ y) {
+  using V = Pair2<F>;
   extern __shared__ __align__(16) unsigned char pi_smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
@@ -556,12 +560,12 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
   const int64_t s0 = block_off[q];
   const int64_t n = (block_off[q + 1] - s0) * nmax;
   const int64_t T = (n + 31) / 32;
-  const float2* A = inv + mat_off[q];
+  const V* A = inv + mat_off[q];
   const int* pp = pivperm + s0 * nmax;
   const Pair2<R>* xr = x + (int64_t)rhs * N * nmax;
   Pair2<R>* yr = y + (int64_t)rhs * N * nmax;
-  float2* xv = reinterpret_cast<float2*>(pi_smem);  // [n] P y
-  float2* tv = xv + n;                              // [n] t = L^{-1} P y
+  V* xv = reinterpret_cast<V*>(pi_smem);  // [n] P y
+  V* tv = xv + n;                         // [n] t = L^{-1} P y
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int NW = kInvThreads / 32;
   for (int64_t t = tid; t < n; t += blockDim.x) {
@@ -569,40 +573,40 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
     const int64_t a = src / nmax;
     const int r = static_cast<int>(src - a * nmax);
     const Pair2<R> e = xr[(int64_t)perm[s0 + a] * nmax + r];
-    xv[t] = make_float2(static_cast<float>(e.re), static_cast<float>(e.im));
+    xv[t] = V{static_cast<F>(e.re), static_cast<F>(e.im)};
   }
   __syncthreads();
-  // row i of a lower (upper) product: sum over columns [j0, j1) of A[i, j] v[j]
-  auto rowdot = [&](int64_t i, int64_t j0, int64_t j1, const float2* v) {
-    float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
-    const float2* a = A + i;
+  // row i: sum over columns [j0, j1) of A[i, j] v[j]
+  auto rowdot = [&](int64_t i, int64_t j0, int64_t j1, const V* v) {
+    F ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
+    const V* a = A + i;
     int64_t jj = j0;
     for (; jj + 8 <= j1; jj += 8) {
-      float2 m[8];
+      V m[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) m[u] = a[(jj + u) * n];
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
-        const float2 v0 = v[jj + u], v1 = v[jj + u + 1];
-        ar0 += m[u].x * v0.x - m[u].y * v0.y;
-        ai0 += m[u].x * v0.y + m[u].y * v0.x;
-        ar1 += m[u + 1].x * v1.x - m[u + 1].y * v1.y;
-        ai1 += m[u + 1].x * v1.y + m[u + 1].y * v1.x;
+        const V v0 = v[jj + u], v1 = v[jj + u + 1];
+        ar0 += m[u].re * v0.re - m[u].im * v0.im;
+        ai0 += m[u].re * v0.im + m[u].im * v0.re;
+        ar1 += m[u + 1].re * v1.re - m[u + 1].im * v1.im;
+        ai1 += m[u + 1].re * v1.im + m[u + 1].im * v1.re;
       }
     }
     for (; jj < j1; ++jj) {
-      const float2 m = a[jj * n], v0 = v[jj];
-      ar0 += m.x * v0.x - m.y * v0.y;
-      ai0 += m.x * v0.y + m.y * v0.x;
+      const V m = a[jj * n], v0 = v[jj];
+      ar0 += m.re * v0.re - m.im * v0.im;
+      ai0 += m.re * v0.im + m.im * v0.re;
     }
-    return make_float2(ar0 + ar1, ai0 + ai1);
+    return V{ar0 + ar1, ai0 + ai1};
   };
   // t = L^{-1} P y on own tiles (unit diagonal), into every CTA's copy of t
   for (int64_t tt = s + (int64_t)C * wid; tt < T; tt += (int64_t)C * NW) {
     const int64_t i = tt * 32 + lane;
     if (i < n) {
-      const float2 d = rowdot(i, 0, i, xv);
-      const float2 t = make_float2(xv[i].x + d.x, xv[i].y + d.y);
+      const V d = rowdot(i, 0, i, xv);
+      const V t = V{xv[i].re + d.re, xv[i].im + d.im};
       for (int dst = 0; dst < C; ++dst) cluster.map_shared_rank(tv, dst)[i] = t;
     }
   }
@@ -611,23 +615,25 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
   for (int64_t tt = s + (int64_t)C * wid; tt < T; tt += (int64_t)C * NW) {
     const int64_t i = tt * 32 + lane;
     if (i < n) {
-      const float2 o = rowdot(i, i, n, tv);
+      const V o = rowdot(i, i, n, tv);
       const int64_t a = i / nmax;
       const int r = static_cast<int>(i - a * nmax);
-      yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(o.x), static_cast<R>(o.y)};
+      yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(o.re), static_cast<R>(o.im)};
     }
   }
 }
 
+// FP64 explicit inverses of L and U of every block (from the FP64 LU and
+// FP64 tile inverses) into inv64
 cudaError_t launch_precond_tri_inverse(int64_t nblocks, int64_t max_tiles, const int64_t* block_off,
-                                       const int64_t* mat_off, const int64_t* tile_off, int nmax, const float* lu32,
-                                       const float* tinv32, float* inv32, cudaStream_t st) {
+                                       const int64_t* mat_off, const int64_t* tile_off, int nmax, const double* lu,
+                                       const double* tinv, double* inv, cudaStream_t st) {
   if (nblocks <= 0 || max_tiles <= 0) return cudaSuccess;
   dim3 grid(static_cast<unsigned>(max_tiles), static_cast<unsigned>(nblocks), 2);
-  precond_tri_inverse_kernel<<<grid, 256, 0, st>>>(block_off, mat_off, tile_off, nmax,
-                                                   reinterpret_cast<const float2*>(lu32),
-                                                   reinterpret_cast<const float2*>(tinv32),
-                                                   reinterpret_cast<float2*>(inv32));
+  precond_tri_inverse_kernel<double><<<grid, 256, 0, st>>>(block_off, mat_off, tile_off, nmax,
+                                                           reinterpret_cast<const Pair2<double>*>(lu),
+                                                           reinterpret_cast<const Pair2<double>*>(tinv),
+                                                           reinterpret_cast<Pair2<double>*>(inv));
   note_launch();
   return cudaGetLastError();
 }
@@ -731,18 +737,19 @@ int precond_cluster_size(double mean_tiles) {
   return 1;
 }
 
-// the FP32 inverse form fits when both block vectors fit in shared memory
+// the two-product form fits when both FP64 block vectors fit in shared memory
 bool precond_inverse_fits(int max_block_dim) {
-  return 2 * sizeof(float2) * static_cast<size_t>(max_block_dim) <= kApplyClusterMaxSmem;
+  return 2 * sizeof(Pair2<double>) * static_cast<size_t>(max_block_dim) <= kApplyClusterMaxSmem;
 }
 
+template <typename R>
 cudaError_t launch_apply_inv(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
-                             const int* perm, const float* inv32, const int* pivperm, int64_t N, int nrhs,
-                             const void* x, void* y, int max_block_dim, int csize, cudaStream_t st) {
+                             const int* perm, const R* inv, const int* pivperm, int64_t N, int nrhs, const void* x,
+                             void* y, int max_block_dim, int csize, cudaStream_t st) {
   static PerDevice attr;
   cudaError_t se = cudaSuccess;
   if (attr.get(current_device, [&] {
-        se = cudaFuncSetAttribute(precond_apply_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        se = cudaFuncSetAttribute(precond_apply_inv_kernel<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kApplyClusterMaxSmem);
         return se == cudaSuccess ? 1 : 0;
       }) == 0)
@@ -750,7 +757,7 @@ cudaError_t launch_apply_inv(int64_t nblocks, const int64_t* block_off, const in
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(nblocks * csize), static_cast<unsigned>(nrhs));
   cfg.blockDim = dim3(kInvThreads);
-  cfg.dynamicSmemBytes = 2 * sizeof(float2) * static_cast<size_t>(max_block_dim);
+  cfg.dynamicSmemBytes = 2 * sizeof(Pair2<R>) * static_cast<size_t>(max_block_dim);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -759,31 +766,33 @@ cudaError_t launch_apply_inv(int64_t nblocks, const int64_t* block_off, const in
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, precond_apply_inv_kernel<float>, block_off, mat_off, nmax, perm,
-                                           reinterpret_cast<const float2*>(inv32), pivperm, N,
-                                           static_cast<const Pair2<float>*>(x), static_cast<Pair2<float>*>(y));
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, precond_apply_inv_kernel<R, R>, block_off, mat_off, nmax, perm,
+                                           reinterpret_cast<const Pair2<R>*>(inv), pivperm, N,
+                                           static_cast<const Pair2<R>*>(x), static_cast<Pair2<R>*>(y));
   note_launch();
   return e;
 }
 
-// FP64 vectors use the FP64 factors; FP32 vectors the FP32 copy (mats32),
-// which holds the explicit inverses of L and U when fp32_inverse is set
-// (the two-product form), else the FP32 LU factors.  With tile inverses
-// (tinv non-null) and a block vector that fits in shared memory, the FP64
-// (and FP32 LU) solves run in the cluster substitution form; otherwise in the
-// one-CTA-per-block form.
+// FP64 vectors use the FP64 factors (mats), FP32 vectors the FP32 copy
+// (mats32).  With `inverse` set both hold the explicit inverses of L and U
+// (the two-product form); otherwise the LU factors, solved by substitution:
+// in the cluster form when tile inverses exist and the block vector fits in
+// shared memory, else one CTA per block.
 template <typename R>
 cudaError_t launch_precond_apply(int64_t nblocks, const int64_t* block_off, const int64_t* mat_off, int nmax,
                                  const int* perm, const double* mats, const float* mats32, const int* piv, int64_t N,
                                  int nrhs, const void* x, void* y, double* work, int max_block_dim, cudaStream_t st,
                                  const int64_t* tile_off, const double* tinv, const float* tinv32, int csize,
-                                 bool fp32_inverse) {
+                                 bool inverse) {
   if (nblocks <= 0) return cudaSuccess;
   constexpr size_t esz = sizeof(R) == 8 ? 16 : 8;
-  if constexpr (sizeof(R) == 4) {
-    if (fp32_inverse)
-      return launch_apply_inv(nblocks, block_off, mat_off, nmax, perm, mats32, piv, N, nrhs, x, y, max_block_dim,
-                              csize >= 1 ? csize : 1, st);
+  if (inverse) {
+    if constexpr (sizeof(R) == 8)
+      return launch_apply_inv<double>(nblocks, block_off, mat_off, nmax, perm, mats, piv, N, nrhs, x, y,
+                                      max_block_dim, csize >= 1 ? csize : 1, st);
+    else
+      return launch_apply_inv<float>(nblocks, block_off, mat_off, nmax, perm, mats32, piv, N, nrhs, x, y,
+                                     max_block_dim, csize >= 1 ? csize : 1, st);
   }
   if (tinv && csize >= 1 && esz * static_cast<size_t>(max_block_dim) <= kApplyClusterMaxSmem) {
     if constexpr (sizeof(R) == 8)
