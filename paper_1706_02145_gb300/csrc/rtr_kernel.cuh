@@ -335,7 +335,11 @@ __device__ __forceinline__ void rot_fwd_row(const R* dv, const R (&xt)[2][2 * l 
   xp(2 * (NH + r) + 1) = b1;
 }
 
-template <int L, int l, typename R, typename XV, int... MUI>
+// PP (packed phase): the x+ half's e^{i m phi} multiply on the packed
+// two-lane FMA, which moves work from the scalar half of the FP32 lanes (that
+// carries the axial entries, the axial apply and the phases) to the half that
+// carries the packed rotations; an autotuner candidate (ConfigAlt at lmax 4)
+template <int L, int l, bool PP, typename R, typename XV, int... MUI>
 __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
                                               std::integer_sequence<int, MUI...>) {
   constexpr int NH = L * (L + 2);
@@ -350,18 +354,25 @@ __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R
     const R ei = m < 0 ? -g.eim[am] : g.eim[am];
     const int r = l * (l + 1) - 1 + m;
     const Pair2<R> xa = xs[r], xb = xs[NH + r];
-    xt[0][mi][0] = fma_(xa.re, er, -xa.im * ei);
-    xt[0][mi][1] = fma_(xa.re, ei, xa.im * er);
+    if constexpr (PP && kPacked<L, R>) {
+      const float2 t = __fmul2_rn(make_float2(xa.im, xa.im), make_float2(-ei, er));
+      const float2 u = __ffma2_rn(make_float2(xa.re, xa.re), make_float2(er, ei), t);
+      xt[0][mi][0] = u.x;
+      xt[0][mi][1] = u.y;
+    } else {
+      xt[0][mi][0] = fma_(xa.re, er, -xa.im * ei);
+      xt[0][mi][1] = fma_(xa.re, ei, xa.im * er);
+    }
     xt[1][mi][0] = fma_(xb.re, er, -xb.im * ei);
     xt[1][mi][1] = fma_(xb.re, ei, xb.im * er);
   }
   (rot_fwd_row<L, l, MUI - l>(dv, xt, xp, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
 }
 
-template <int L, typename R, typename XV, int... LI>
+template <int L, bool PP, typename R, typename XV, int... LI>
 __device__ __forceinline__ void rot_fwd(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
                                         std::integer_sequence<int, LI...>) {
-  (rot_fwd_block<L, LI + 1>(g, xs, xp, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+  (rot_fwd_block<L, LI + 1, PP>(g, xs, xp, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
 }
 
 // ---- step 3: axial translation --------------------------------------------
@@ -648,9 +659,9 @@ struct RowAccSmem {
   __device__ __forceinline__ void store(int r, const R (&c)[4]) const { a[r * BLOCK] = Quad4<R>{c[0], c[1], c[2], c[3]}; }
 };
 
-template <int L, bool INPLACE, bool SYM, typename R, typename XV, typename YV, typename Acc>
+template <int L, bool INPLACE, bool SYM, typename R, bool PP = false, typename XV, typename YV, typename Acc>
 __device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, YV& yp, Acc& acc) {
-  rot_fwd<L>(g, xs, xp, std::make_integer_sequence<int, L>{});
+  rot_fwd<L, PP>(g, xs, xp, std::make_integer_sequence<int, L>{});
   axial<L, INPLACE, SYM>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
   rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
 }
@@ -666,7 +677,7 @@ __device__ __forceinline__ void pair_lazy(const GeomS& q, const Pair2<float>* __
   {
     Geom<L, float> g;
     geometry_angles<L>(q.ct, q.st, q.cph, q.sph, g);
-    rot_fwd<L>(g, xs, xp, std::make_integer_sequence<int, L>{});
+    rot_fwd<L, false>(g, xs, xp, std::make_integer_sequence<int, L>{});
   }
   {
     Geom<L, float> g;
@@ -699,17 +710,19 @@ struct Config {
   static constexpr bool LAZY_GEOM = !FP64 && L == 5;
   static constexpr bool SYNC_PAIR = false;  // barrier per source (keeps a CTA's warps in step)
   static constexpr int MINB = (!FP64 && L == 3) ? 3 : 1;  // minimum resident CTAs per SM for the allocator
+  static constexpr bool PACK_PHASE = false;  // x+ phase multiply on the packed FMA (rot_fwd_block)
 };
 
 // The alternative FP32 launch shape of each lmax, the second candidate of
 // the autotuner (celes_ctx tuning): lmax 1-2 64-receiver CTAs, lmax 3 the
-// register allocator left free (two CTAs per SM), lmax 4 64-source tiles,
-// lmax 5 64-receiver CTAs.  Everything else as in Config.
+// register allocator left free (two CTAs per SM), lmax 4 the x+ phase
+// multiply on the packed FMA, lmax 5 64-receiver CTAs.  Everything else as in
+// Config.
 template <int L, typename R>
 struct ConfigAlt : Config<L, R> {
   static constexpr int BLOCK = (L <= 2 || L == 5) ? 64 : 128;
-  static constexpr int TJ = L == 4 ? 64 : 32;
   static constexpr int MINB = 1;
+  static constexpr bool PACK_PHASE = L == 4;
 };
 
 template <int L, typename R, typename C = Config<L, R>>
@@ -801,11 +814,11 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
           if constexpr (C::ACC_SMEM) {
             RowAccSmem<R, BLOCK> acc{sacc4 + tid};
             if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL>(gs, xs, xp, yp, acc);
-            else pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R, C::PACK_PHASE>(g, xs, xp, yp, acc);
           } else {
             RowAccReg<R> acc{areg};
             if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL>(gs, xs, xp, yp, acc);
-            else pair<L, INPL, C::SYM_AXIAL, R>(g, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R, C::PACK_PHASE>(g, xs, xp, yp, acc);
           }
         };
         if constexpr (C::XY_SMEM) {
