@@ -33,6 +33,11 @@ namespace rtr {
 // the stack (8.7 vs 4.1 ms at N = 4000), so lmax 5 keeps the scalar form.
 template <int L, typename R>
 constexpr bool kPacked = std::is_same<R, float>::value && L <= 4;
+// launch-shape option bits of the pair code: 1 = the x+ phase multiply on the
+// packed FMA, 2 = packed rotations at every lmax (lmax 5 with x' and y' in
+// shared memory has the registers for them)
+template <int L, typename R, int OPT>
+constexpr bool kPackedRot = std::is_same<R, float>::value && (L <= 4 || (OPT & 2) != 0);
 
 template <typename R>
 struct alignas(4 * sizeof(R)) Quad4 {
@@ -293,12 +298,12 @@ struct Row {
 
 // ---- step 2: x'[l, MU] = sum_M R_{MU,M} e^{i M phi} x[l, M] ----------------
 // x~ (rotated about z) of degree l held in xt[2][2l+1][2]
-template <int L, int l, int MU, typename R, typename XV, int... MI>
+template <int L, int l, int MU, int OPT, typename R, typename XV, int... MI>
 __device__ __forceinline__ void rot_fwd_row(const R* dv, const R (&xt)[2][2 * l + 1][2], XV& xp,
                                             std::integer_sequence<int, MI...>) {
   constexpr int NH = L * (L + 2);
   R a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-  if constexpr (kPacked<L, R>) {
+  if constexpr (kPackedRot<L, R, OPT>) {
     // (re, im) of one complex value per packed FMA, same rounding as fma_
     float2 a = make_float2(0.0f, 0.0f), b = a;
     (
@@ -339,7 +344,7 @@ __device__ __forceinline__ void rot_fwd_row(const R* dv, const R (&xt)[2][2 * l 
 // two-lane FMA, which moves work from the scalar half of the FP32 lanes (that
 // carries the axial entries, the axial apply and the phases) to the half that
 // carries the packed rotations; an autotuner candidate (ConfigAlt at lmax 4)
-template <int L, int l, bool PP, typename R, typename XV, int... MUI>
+template <int L, int l, int OPT, typename R, typename XV, int... MUI>
 __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
                                               std::integer_sequence<int, MUI...>) {
   constexpr int NH = L * (L + 2);
@@ -354,7 +359,7 @@ __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R
     const R ei = m < 0 ? -g.eim[am] : g.eim[am];
     const int r = l * (l + 1) - 1 + m;
     const Pair2<R> xa = xs[r], xb = xs[NH + r];
-    if constexpr (PP && kPacked<L, R>) {
+    if constexpr ((OPT & 1) != 0 && kPackedRot<L, R, OPT>) {
       const float2 t = __fmul2_rn(make_float2(xa.im, xa.im), make_float2(-ei, er));
       const float2 u = __ffma2_rn(make_float2(xa.re, xa.re), make_float2(er, ei), t);
       xt[0][mi][0] = u.x;
@@ -366,13 +371,13 @@ __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R
     xt[1][mi][0] = fma_(xb.re, er, -xb.im * ei);
     xt[1][mi][1] = fma_(xb.re, ei, xb.im * er);
   }
-  (rot_fwd_row<L, l, MUI - l>(dv, xt, xp, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
+  (rot_fwd_row<L, l, MUI - l, OPT>(dv, xt, xp, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
 }
 
-template <int L, bool PP, typename R, typename XV, int... LI>
+template <int L, int OPT, typename R, typename XV, int... LI>
 __device__ __forceinline__ void rot_fwd(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
                                         std::integer_sequence<int, LI...>) {
-  (rot_fwd_block<L, LI + 1, PP>(g, xs, xp, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+  (rot_fwd_block<L, LI + 1, OPT>(g, xs, xp, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
 }
 
 // ---- step 3: axial translation --------------------------------------------
@@ -550,12 +555,12 @@ __device__ __forceinline__ void axial(const Geom<L, R>& g, XV& xp, YV& yp, std::
 }
 
 // ---- step 4: y[l, M] += e^{-i M phi} sum_MU R_{MU,M} y'[l, MU] -------------
-template <int L, int l, int M, typename R, typename YV, typename Acc, int... MUI>
+template <int L, int l, int M, int OPT, typename R, typename YV, typename Acc, int... MUI>
 __device__ __forceinline__ void rot_bwd_col(const Geom<L, R>& g, const R* dv, YV& yp, Acc& acc,
                                             std::integer_sequence<int, MUI...>) {
   constexpr int NH = L * (L + 2);
   R a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-  if constexpr (kPacked<L, R>) {
+  if constexpr (kPackedRot<L, R, OPT>) {
     float2 a = make_float2(0.0f, 0.0f), b = a;
     (
         [&] {
@@ -601,17 +606,17 @@ __device__ __forceinline__ void rot_bwd_col(const Geom<L, R>& g, const R* dv, YV
   (void)NH;
 }
 
-template <int L, int l, typename R, typename YV, typename Acc, int... MI>
+template <int L, int l, int OPT, typename R, typename YV, typename Acc, int... MI>
 __device__ __forceinline__ void rot_bwd_block(const Geom<L, R>& g, YV& yp, Acc& acc,
                                               std::integer_sequence<int, MI...>) {
   R dv[DCount<l>::ncanon];
   dmatrix<L, l>(g, dv);
-  (rot_bwd_col<L, l, MI - l>(g, dv, yp, acc, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
+  (rot_bwd_col<L, l, MI - l, OPT>(g, dv, yp, acc, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
 }
 
-template <int L, typename R, typename YV, typename Acc, int... LI>
+template <int L, int OPT, typename R, typename YV, typename Acc, int... LI>
 __device__ __forceinline__ void rot_bwd(const Geom<L, R>& g, YV& yp, Acc& acc, std::integer_sequence<int, LI...>) {
-  (rot_bwd_block<L, LI + 1>(g, yp, acc, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+  (rot_bwd_block<L, LI + 1, OPT>(g, yp, acc, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
 }
 
 // storage views: registers (compile-time index) or a per-thread column of a
@@ -659,11 +664,11 @@ struct RowAccSmem {
   __device__ __forceinline__ void store(int r, const R (&c)[4]) const { a[r * BLOCK] = Quad4<R>{c[0], c[1], c[2], c[3]}; }
 };
 
-template <int L, bool INPLACE, bool SYM, typename R, bool PP = false, typename XV, typename YV, typename Acc>
+template <int L, bool INPLACE, bool SYM, typename R, int OPT = 0, typename XV, typename YV, typename Acc>
 __device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, YV& yp, Acc& acc) {
-  rot_fwd<L, PP>(g, xs, xp, std::make_integer_sequence<int, L>{});
+  rot_fwd<L, OPT>(g, xs, xp, std::make_integer_sequence<int, L>{});
   axial<L, INPLACE, SYM>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
-  rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
+  rot_bwd<L, OPT>(g, yp, acc, std::make_integer_sequence<int, L>{});
 }
 
 // One pair with the tables rebuilt per stage from the pair's scalars: the
@@ -671,13 +676,13 @@ __device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __rest
 // step.  The rebuild before the backward rotation reads the scalars through
 // an optimizer barrier, so the compiler cannot keep the forward rotation's
 // tables alive across the axial step (fewer live registers per thread).
-template <int L, bool INPLACE, bool SYM, typename XV, typename YV, typename Acc>
+template <int L, bool INPLACE, bool SYM, int OPT = 0, typename XV, typename YV, typename Acc>
 __device__ __forceinline__ void pair_lazy(const GeomS& q, const Pair2<float>* __restrict__ xs, XV& xp, YV& yp,
                                           Acc& acc) {
   {
     Geom<L, float> g;
     geometry_angles<L>(q.ct, q.st, q.cph, q.sph, g);
-    rot_fwd<L, false>(g, xs, xp, std::make_integer_sequence<int, L>{});
+    rot_fwd<L, OPT>(g, xs, xp, std::make_integer_sequence<int, L>{});
   }
   {
     Geom<L, float> g;
@@ -689,7 +694,7 @@ __device__ __forceinline__ void pair_lazy(const GeomS& q, const Pair2<float>* __
   {
     Geom<L, float> g;
     geometry_angles<L>(ct, st, cph, sph, g);
-    rot_bwd<L>(g, yp, acc, std::make_integer_sequence<int, L>{});
+    rot_bwd<L, OPT>(g, yp, acc, std::make_integer_sequence<int, L>{});
   }
 }
 
@@ -710,19 +715,22 @@ struct Config {
   static constexpr bool LAZY_GEOM = !FP64 && L == 5;
   static constexpr bool SYNC_PAIR = false;  // barrier per source (keeps a CTA's warps in step)
   static constexpr int MINB = (!FP64 && L == 3) ? 3 : 1;  // minimum resident CTAs per SM for the allocator
-  static constexpr bool PACK_PHASE = false;  // x+ phase multiply on the packed FMA (rot_fwd_block)
+  static constexpr int OPT = 0;  // pair-code option bits (kPackedRot)
 };
 
 // The alternative FP32 launch shape of each lmax, the second candidate of
 // the autotuner (celes_ctx tuning): lmax 1-2 64-receiver CTAs, lmax 3 the
 // register allocator left free (two CTAs per SM), lmax 4 the x+ phase
-// multiply on the packed FMA, lmax 5 64-receiver CTAs.  Everything else as in
-// Config.
+// multiply on the packed FMA, lmax 5 64-receiver CTAs with x' and y' in shared
+// memory (in place) and the rotations on the packed FMA.  Everything else as
+// in Config.
 template <int L, typename R>
 struct ConfigAlt : Config<L, R> {
   static constexpr int BLOCK = (L <= 2 || L == 5) ? 64 : 128;
   static constexpr int MINB = 1;
-  static constexpr bool PACK_PHASE = L == 4;
+  static constexpr int OPT = L == 4 ? 1 : (L == 5 ? 2 : 0);
+  static constexpr bool XY_SMEM = Config<L, R>::XY_SMEM || L == 5;
+  static constexpr bool XY_INPLACE = XY_SMEM;
 };
 
 template <int L, typename R, typename C = Config<L, R>>
@@ -813,12 +821,12 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
           constexpr bool INPL = C::XY_SMEM && C::XY_INPLACE;
           if constexpr (C::ACC_SMEM) {
             RowAccSmem<R, BLOCK> acc{sacc4 + tid};
-            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL>(gs, xs, xp, yp, acc);
-            else pair<L, INPL, C::SYM_AXIAL, R, C::PACK_PHASE>(g, xs, xp, yp, acc);
+            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL, C::OPT>(gs, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R, C::OPT>(g, xs, xp, yp, acc);
           } else {
             RowAccReg<R> acc{areg};
-            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL>(gs, xs, xp, yp, acc);
-            else pair<L, INPL, C::SYM_AXIAL, R, C::PACK_PHASE>(g, xs, xp, yp, acc);
+            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL, C::OPT>(gs, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R, C::OPT>(g, xs, xp, yp, acc);
           }
         };
         if constexpr (C::XY_SMEM) {
