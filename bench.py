@@ -991,8 +991,12 @@ def run_case(args):
     else:
         pairs = sc.N * (sc.N - 1) * nrhs
         shape = B.celes_coupling_shape(ctx, prec) if args.kernel != "direct" else None
+        kern_id = B.CELES_KERNEL_DIRECT if args.kernel == "direct" else B.CELES_KERNEL_RTR
+        tflops = B.celes_flops_per_pair(sc.lmax, kern_id) * pairs / t / 1e12
+        peak, _ = B.celes_fma_peak(B.FMA_FP32 if prec == B.CELES_FP32 else B.FMA_FP64)
         print(f"N={sc.N} lmax={sc.lmax} {args.precision} kernel={args.kernel} rhs={nrhs}: {t * 1e3:.3f} ms, "
-              f"{pairs / t:.3e} couplings/s, shape (variant, chunks, tuned ms) {shape}")
+              f"{pairs / t:.3e} couplings/s, {tflops:.1f} TFLOP/s = {tflops / peak:.3f} of the measured "
+              f"{peak:.1f}, shape (variant, chunks, tuned ms) {shape}")
     B.celes_destroy(ctx)
 
 
