@@ -72,8 +72,10 @@ typedef struct {
                            on this problem (cached per device, lmax, precision and size class) and
                            keeps the fastest; it synchronises, so make that first product before
                            any stream capture.  0: the built-in shape, about eight waves of chunks */
-  int variant;          /* -1 (default): as autotune decides; 0 or 1: force the FP32 launch shape
-                           (0 = built-in, 1 = the alternative); FP64 always uses the built-in one */
+  int variant;          /* -1 (default): as autotune decides; 0..3 force the launch shape: bit 0 the
+                           FP32 compile-time shape (0 = built-in, 1 = the alternative; FP64 always
+                           uses the built-in one), bit 1 the cluster reduction of the partial sums
+                           (thread-block clusters of up to 8 source chunks) */
 } celes_options;
 
 typedef enum { CELES_PLANE_WAVE = 0, CELES_GAUSSIAN_BEAM = 1 } celes_incident_kind;
@@ -170,7 +172,8 @@ int celes_master_matvec(celes_ctx* ctx, const void* x, void* y, int nrhs, int pr
 int celes_precond_build(celes_ctx* ctx, double cuboid_edge);
 
 /* Launch shape the context's coupling kernel uses in `precision`: variant
- * (0 built-in, 1 alternative FP32 shape), source chunks per product and, if
+ * (bit 0: alternative FP32 shape; bit 1: cluster reduction of the partial
+ * sums, see celes_options.variant), source chunks per product and, if
  * the autotuner chose it, the timed duration of the winning candidate (ms; 0
  * otherwise).  CELES_ESTATE before the first coupling product in that
  * precision.  Measurement support; the paper has no counterpart. */

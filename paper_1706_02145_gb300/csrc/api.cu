@@ -34,17 +34,17 @@ namespace celes {
                                             void* partial, double k, int chunks, cudaStream_t st);         \
   int coupling_rpb_##LL(int precision);                                                                    \
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
-                                       void* partial, double k, int chunks, cudaStream_t st);              \
+                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl);   \
   int coupling_rtr_rpb_##LL(int precision);                                                                \
-  int coupling_rtr_slices_##LL(int precision, int chunks);                                                 \
+  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl);                                      \
   int coupling_rtr_slots_##LL(int precision);                                                              \
   long long coupling_rtr_flops_##LL();                                                                     \
   int coupling_terms_export_##LL(int* idx, double* val, int cap);
 #define CELES_DECLARE_ALT(LL)                                                                              \
   cudaError_t launch_coupling_rtr_alt_##LL(int64_t N, const void* pos, const void* x, void* partial,       \
-                                           double k, int chunks, cudaStream_t st);                         \
+                                           double k, int chunks, cudaStream_t st, int maxcl);              \
   int coupling_rtr_alt_rpb_##LL();                                                                         \
-  int coupling_rtr_alt_slices_##LL(int chunks);                                                            \
+  int coupling_rtr_alt_slices_##LL(int chunks, int maxcl);                                                 \
   int coupling_rtr_alt_slots_##LL();
 CELES_DECLARE_ALT(1)
 CELES_DECLARE_ALT(2)
@@ -71,35 +71,38 @@ cudaError_t launch_coupling_partial(int L, int precision, int64_t N, const void*
   }
 }
 cudaError_t launch_coupling_rtr(int L, int precision, int64_t N, const void* pos, const void* x, void* partial,
-                                double k, int chunks, cudaStream_t st) {
+                                double k, int chunks, cudaStream_t st, int maxcl = 1) {
   switch (L) {
-    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st);
-    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st);
-    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st);
-    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st);
-    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st);
+    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st, maxcl);
+    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st, maxcl);
+    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st, maxcl);
+    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st, maxcl);
+    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st, maxcl);
     default: return cudaErrorInvalidValue;
   }
 }
 int coupling_rtr_receivers_per_block(int L, int precision);
 int coupling_rtr_slots(int L, int precision);
 
-// launch shape `variant` (0: Config, 1: ConfigAlt, FP32 only)
+// launch shape `variant`: bit 0 the compile-time shape (0: Config, 1:
+// ConfigAlt, FP32 only), bit 1 the cluster reduction of the partial sums
+// (clusters of up to 8 chunks)
 cudaError_t launch_coupling_rtr_v(int L, int precision, int variant, int64_t N, const void* pos, const void* x,
                                   void* partial, double k, int chunks, cudaStream_t st) {
-  if (variant == 0 || precision == CELES_FP64)
-    return launch_coupling_rtr(L, precision, N, pos, x, partial, k, chunks, st);
+  const int maxcl = (variant & 2) ? 8 : 1;
+  if ((variant & 1) == 0 || precision == CELES_FP64)
+    return launch_coupling_rtr(L, precision, N, pos, x, partial, k, chunks, st, maxcl);
   switch (L) {
-    case 1: return launch_coupling_rtr_alt_1(N, pos, x, partial, k, chunks, st);
-    case 2: return launch_coupling_rtr_alt_2(N, pos, x, partial, k, chunks, st);
-    case 3: return launch_coupling_rtr_alt_3(N, pos, x, partial, k, chunks, st);
-    case 4: return launch_coupling_rtr_alt_4(N, pos, x, partial, k, chunks, st);
-    case 5: return launch_coupling_rtr_alt_5(N, pos, x, partial, k, chunks, st);
+    case 1: return launch_coupling_rtr_alt_1(N, pos, x, partial, k, chunks, st, maxcl);
+    case 2: return launch_coupling_rtr_alt_2(N, pos, x, partial, k, chunks, st, maxcl);
+    case 3: return launch_coupling_rtr_alt_3(N, pos, x, partial, k, chunks, st, maxcl);
+    case 4: return launch_coupling_rtr_alt_4(N, pos, x, partial, k, chunks, st, maxcl);
+    case 5: return launch_coupling_rtr_alt_5(N, pos, x, partial, k, chunks, st, maxcl);
     default: return cudaErrorInvalidValue;
   }
 }
 int coupling_rtr_rpb_v(int L, int precision, int variant) {
-  if (variant == 0 || precision == CELES_FP64) return coupling_rtr_receivers_per_block(L, precision);
+  if ((variant & 1) == 0 || precision == CELES_FP64) return coupling_rtr_receivers_per_block(L, precision);
   switch (L) {
     case 1: return coupling_rtr_alt_rpb_1();
     case 2: return coupling_rtr_alt_rpb_2();
@@ -112,27 +115,28 @@ int coupling_rtr_rpb_v(int L, int precision, int variant) {
 // partial-sum slices a launch with `chunks` source chunks writes (the
 // cluster reduction of the shared-memory accumulator shapes divides it)
 int coupling_rtr_slices_v(int L, int precision, int variant, int chunks) {
-  if (variant == 0 || precision == CELES_FP64) {
+  const int maxcl = (variant & 2) ? 8 : 1;
+  if ((variant & 1) == 0 || precision == CELES_FP64) {
     switch (L) {
-      case 1: return coupling_rtr_slices_1(precision, chunks);
-      case 2: return coupling_rtr_slices_2(precision, chunks);
-      case 3: return coupling_rtr_slices_3(precision, chunks);
-      case 4: return coupling_rtr_slices_4(precision, chunks);
-      case 5: return coupling_rtr_slices_5(precision, chunks);
+      case 1: return coupling_rtr_slices_1(precision, chunks, maxcl);
+      case 2: return coupling_rtr_slices_2(precision, chunks, maxcl);
+      case 3: return coupling_rtr_slices_3(precision, chunks, maxcl);
+      case 4: return coupling_rtr_slices_4(precision, chunks, maxcl);
+      case 5: return coupling_rtr_slices_5(precision, chunks, maxcl);
       default: return chunks;
     }
   }
   switch (L) {
-    case 1: return coupling_rtr_alt_slices_1(chunks);
-    case 2: return coupling_rtr_alt_slices_2(chunks);
-    case 3: return coupling_rtr_alt_slices_3(chunks);
-    case 4: return coupling_rtr_alt_slices_4(chunks);
-    case 5: return coupling_rtr_alt_slices_5(chunks);
+    case 1: return coupling_rtr_alt_slices_1(chunks, maxcl);
+    case 2: return coupling_rtr_alt_slices_2(chunks, maxcl);
+    case 3: return coupling_rtr_alt_slices_3(chunks, maxcl);
+    case 4: return coupling_rtr_alt_slices_4(chunks, maxcl);
+    case 5: return coupling_rtr_alt_slices_5(chunks, maxcl);
     default: return chunks;
   }
 }
 int coupling_rtr_slots_v(int L, int precision, int variant) {
-  if (variant == 0 || precision == CELES_FP64) return coupling_rtr_slots(L, precision);
+  if ((variant & 1) == 0 || precision == CELES_FP64) return coupling_rtr_slots(L, precision);
   switch (L) {
     case 1: return coupling_rtr_alt_slots_1();
     case 2: return coupling_rtr_alt_slots_2();
@@ -392,10 +396,12 @@ int autotune(celes_ctx* c, int precision, const void* x, cudaStream_t st) {
   if (!have) {
     const size_t elem = precision == CELES_FP64 ? 16 : 8;
     const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
-    const int nvar = precision == CELES_FP64 ? 1 : 2;
+    // shapes: FP32 built-in / alternative, each without and with the
+    // cluster reduction of the partial sums; FP64 built-in with and without
+    std::vector<int> vars = precision == CELES_FP64 ? std::vector<int>{0, 2} : std::vector<int>{0, 1, 2, 3};
     const double waves[3] = {4.0, 8.0, 16.0};
     int maxch = 1;
-    for (int v = 0; v < nvar; ++v)
+    for (int v : vars)
       for (double w : waves) maxch = std::max(maxch, chunks_for(c, Nt, precision, v, w));
     CK(c->partial.ensure(per * std::max(maxch, 1)), "coupling scratch");
     cudaEvent_t a = nullptr, b = nullptr;
@@ -406,7 +412,8 @@ int autotune(celes_ctx* c, int precision, const void* x, cudaStream_t st) {
     }
     best.ms = 1e300;
     cudaError_t e = cudaSuccess;
-    for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
+    for (int v : vars) {
+      if (e != cudaSuccess) break;
       for (double w : waves) {
         const int ch = chunks_for(c, Nt, precision, v, w);
         // one untimed launch (first use of the shape on this device), then one timed
@@ -556,8 +563,8 @@ extern "C" int celes_create(celes_ctx** out, int64_t N, const double* positions,
   c->autotune = opt ? opt->autotune : 1;
   if (opt && opt->variant >= 0) {
     // a forced launch shape (tests and measurements); the chunks as usual
-    if (opt->variant > 1) return CELES_EINVAL;
-    c->tune_variant[0] = 0;
+    if (opt->variant > 3) return CELES_EINVAL;
+    c->tune_variant[0] = opt->variant & 2;
     c->tune_variant[1] = opt->variant;
   }
   if (c->kernel < CELES_KERNEL_AUTO || c->kernel > CELES_KERNEL_RTR) return CELES_EINVAL;

@@ -990,12 +990,12 @@ int resident_slots() {
 // cluster size of the partial-sum reduction for `chunks` source chunks: the
 // largest of 8, 4, 2 that divides it (shared-memory accumulators only), else 1
 template <int L, typename R, typename C = Config<L, R>>
-int partial_cluster(int chunks) {
+int partial_cluster(int chunks, int maxcl) {
   if constexpr (!C::ACC_SMEM) {
     return 1;
   } else {
     for (int c = 8; c > 1; c >>= 1)
-      if (chunks % c == 0) return c;
+      if (c <= maxcl && chunks % c == 0) return c;
     return 1;
   }
 }
@@ -1012,11 +1012,12 @@ int partial_cluster_occupancy() {
   }
 }
 
-// `chunks` source chunks; writes chunks / partial_cluster(chunks) partial
-// slices (the count the epilogue must add)
+// `chunks` source chunks, partial-sum clusters of at most `maxcl` CTAs (1:
+// no cluster reduction); writes chunks / partial_cluster(chunks, maxcl)
+// partial slices (the count the epilogue must add)
 template <int L, typename R, typename C = Config<L, R>>
 cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
-                           cudaStream_t st) {
+                           cudaStream_t st, int maxcl = 1) {
   using LY = Layout<L, R, C>;
   const int occ = partial_occupancy<L, R, C>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -1024,7 +1025,7 @@ cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* part
   if (chunks < 1) chunks = 1;
   const int64_t chunk = (N + chunks - 1) / chunks;
   dim3 grid(static_cast<unsigned>((N + C::BLOCK - 1) / C::BLOCK), static_cast<unsigned>(chunks));
-  const int ncl = partial_cluster<L, R, C>(chunks);
+  const int ncl = partial_cluster<L, R, C>(chunks, maxcl);
   if constexpr (C::ACC_SMEM) {
     if (ncl > 1) {
       if (partial_cluster_occupancy<L, R, C>() < 1) return cudaErrorInvalidConfiguration;

@@ -255,11 +255,14 @@ def test_preconditioner_apply_large_blocks(N, L, edge):
         B.celes_destroy(ctx)
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("N,L,poly,n", CLUSTERS)
-def test_coupling_alternative_fp32_shape(N, L, poly, n):
-    # the autotuner's second FP32 launch shape, forced, against the dense W
+def test_coupling_alternative_fp32_shape(N, L, poly, n, variant):
+    # the autotuner's other FP32 launch shapes, forced, against the dense W:
+    # the alternative compile-time shape (1), the cluster reduction of the
+    # partial sums (2) and both (3)
     sc = synth.random_cluster(23, N + L, N, L, radius=100.0, fill=0.25, n=n, polydisperse=poly)
-    ctx = make_ctx(sc, variant=1)
+    ctx = make_ctx(sc, variant=variant)
     try:
         W = translation.coupling_matrix(sc.positions, sc.k, L)
         x = synth.random_vector(23, 200 + N, (sc.N, sc.nmax))
@@ -270,7 +273,33 @@ def test_coupling_alternative_fp32_shape(N, L, poly, n):
         else:
             assert rel(y, y_ref) < 1e-5
         v, ch, _ = B.celes_coupling_shape(ctx, B.CELES_FP32)
-        assert v == 1 and ch >= 1
+        assert v == variant and ch >= 1
+        if variant & 2:  # the FP64 kernel takes the cluster reduction too
+            y64 = gpu_matvec(ctx, x, B.CELES_FP64)
+            if N == 1:
+                assert np.all(y64 == 0)
+            else:
+                assert rel(y64, y_ref) < 1e-10
+    finally:
+        B.celes_destroy(ctx)
+
+
+@pytest.mark.parametrize("N,L,variant", [(333, 3, 2), (700, 4, 2), (700, 4, 3), (517, 5, 3), (450, 2, 2)])
+def test_coupling_cluster_reduction_on_sampled_rows(N, L, variant):
+    # enough spheres for several source chunks per receiver block, so that the
+    # partial sums really are added in clusters of CTAs; ragged block counts
+    sc = synth.config2(0, N=N, lmax=L)
+    ctx = make_ctx(sc, variant=variant)
+    try:
+        x = synth.random_vector(27, N + L, (sc.N, sc.nmax))
+        rows = [0, 1, N // 3, N // 2 + 1, N - 2, N - 1]
+        ref = translation.coupling_matvec_rows(sc.positions, sc.k, L, x, rows)
+        y32 = gpu_matvec(ctx, x, B.CELES_FP32)
+        _, ch, _ = B.celes_coupling_shape(ctx, B.CELES_FP32)
+        assert ch >= 4 and ch % 4 == 0
+        assert rel(y32[rows], ref) < 1e-5
+        y64 = gpu_matvec(ctx, x, B.CELES_FP64)
+        assert rel(y64[rows], ref) < 1e-10
     finally:
         B.celes_destroy(ctx)
 
