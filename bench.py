@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-ensemble measurement")
     ap.add_argument("--batched-ensembles", type=int, default=64)
     ap.add_argument("--batched-rhs", type=int, default=8)
+    ap.add_argument("--batched-restart", type=int, default=100, help="GMRES restart of both batched forms")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="sphere counts of the multi-ensemble workload times this factor (1 = as stated)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess measurement")
@@ -298,7 +299,7 @@ def run_batched(args, local_rank):
             ctxs.append(c)
             B.celes_set_incident(c, [B.make_incident("plane", beta=i.beta, alpha=i.alpha, pol=i.pol)
                                      for i in sc.incidents])
-        bt = B.celes_batch_create(ctxs, restart=30)
+        bt = B.celes_batch_create(ctxs, restart=args.batched_restart)
         try:
             n = B.celes_batch_num_unknowns(bt)
             x = torch.ones(n, dtype=torch.complex64, device=f"cuda:{local_rank}")
@@ -312,7 +313,8 @@ def run_batched(args, local_rank):
             torch.cuda.synchronize()
             t_mv = (time.perf_counter() - t0) / reps
             pairs = sum(sc.N * (sc.N - 1) * len(sc.incidents) for sc in scenes)
-            code, infos = B.celes_batch_solve(bt, len(ctxs), TOL, mode=B.CELES_SOLVE_MIXED, restart=30,
+            code, infos = B.celes_batch_solve(bt, len(ctxs), TOL, mode=B.CELES_SOLVE_MIXED,
+                                              restart=args.batched_restart, max_iter=20000,
                                               raise_on_noconv=False)
             t_batch = max(i["seconds"] for i in infos)
             res_batch = max(i["residual"] for i in infos)
@@ -322,8 +324,9 @@ def run_batched(args, local_rank):
             B.celes_batch_destroy(bt)
         t_one, res_one, err = 0.0, 0.0, 0.0
         for c, bb in zip(ctxs, b_batch):
-            info = B.celes_solve(c, TOL, mode=B.CELES_SOLVE_MIXED, restart=30, use_precond=False,
-                                 raise_on_noconv=False)
+            # the iteration budget of celes_solve covers all RHS of the context
+            info = B.celes_solve(c, TOL, mode=B.CELES_SOLVE_MIXED, restart=args.batched_restart, use_precond=False,
+                                 max_iter=20000 * args.batched_rhs, raise_on_noconv=False)
             t_one += info["seconds"]
             res_one = max(res_one, info["residual"])
             b1 = B.celes_get_coefficients(c)
@@ -337,7 +340,8 @@ def run_batched(args, local_rank):
                 "batched_solve_s": t_batch, "batched_max_iterations": its_batch, "batched_max_residual": res_batch,
                 "one_by_one_solve_s": t_one, "one_by_one_max_residual": res_one, "speedup": t_one / t_batch,
                 "batched_vs_one_by_one_max_rel_l2": err,
-                "note": "mixed FP32/FP64 GMRES(30) to 1e-6, no preconditioner, first iterate T a, both forms"}
+                "restart": args.batched_restart,
+                "note": "mixed FP32/FP64 restarted GMRES to 1e-6, no preconditioner, first iterate T a, both forms"}
     finally:
         for c in ctxs:
             B.celes_destroy(c)

@@ -576,11 +576,25 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
     xv[t] = V{static_cast<F>(e.re), static_cast<F>(e.im)};
   }
   __syncthreads();
-  // row i: sum over columns [j0, j1) of A[i, j] v[j]
+  // row i: sum over columns [j0, j1) of A[i, j] v[j]; 16 factor loads in
+  // flight per thread
   auto rowdot = [&](int64_t i, int64_t j0, int64_t j1, const V* v) {
     F ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
     const V* a = A + i;
     int64_t jj = j0;
+    for (; jj + 16 <= j1; jj += 16) {
+      V m[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) m[u] = a[(jj + u) * n];
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) {
+        const V v0 = v[jj + u], v1 = v[jj + u + 1];
+        ar0 += m[u].re * v0.re - m[u].im * v0.im;
+        ai0 += m[u].re * v0.im + m[u].im * v0.re;
+        ar1 += m[u + 1].re * v1.re - m[u + 1].im * v1.im;
+        ai1 += m[u + 1].re * v1.im + m[u + 1].im * v1.re;
+      }
+    }
     for (; jj + 8 <= j1; jj += 8) {
       V m[8];
 #pragma unroll
@@ -754,10 +768,20 @@ cudaError_t launch_apply_inv(int64_t nblocks, const int64_t* block_off, const in
         return se == cudaSuccess ? 1 : 0;
       }) == 0)
     return se != cudaSuccess ? se : cudaErrorInvalidConfiguration;
+  // CTAs per block: up to `csize`, but no more than keep every CTA of the
+  // launch resident at once (a partial second wave would double the time)
+  const size_t smem = 2 * sizeof(Pair2<R>) * static_cast<size_t>(max_block_dim);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, precond_apply_inv_kernel<R, R>, kInvThreads, smem) !=
+          cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const int64_t slots = static_cast<int64_t>(occ) * device_sms();
+  while (csize > 1 && nblocks * nrhs * csize > slots) --csize;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(nblocks * csize), static_cast<unsigned>(nrhs));
   cfg.blockDim = dim3(kInvThreads);
-  cfg.dynamicSmemBytes = 2 * sizeof(Pair2<R>) * static_cast<size_t>(max_block_dim);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
