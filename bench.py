@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--c5", action="store_true",
                     help="run only the 100 000-sphere workload end to end (preconditioned mixed solve to 1e-6)")
     ap.add_argument("--c5-edge", type=float, default=1000.0, help="--c5: preconditioner cuboid edge (nm)")
+    ap.add_argument("--plain-full-only", action="store_true",
+                    help="run only the uncapped plain FP64 solve of the bench workload beside the chosen form")
     ap.add_argument("--case", choices=["coupling", "precond", "batch"], default=None,
                     help="run one operation on a synthetic case and print its time (profiling); see run_case")
     ap.add_argument("--lmax", type=int, default=4, help="--case: degree")
@@ -568,6 +570,40 @@ def run_c5(args, local_rank):
     return out
 
 
+def run_plain_full(args, local_rank):
+    """The plain FP64 GMRES solve of the full bench workload to 1e-6,
+    uncapped (about 10 min), beside the chosen form (FP32 inner GMRES with
+    FP64 refinement) on the same context; both errors against the same
+    system refined to 1e-10."""
+    import synth
+    from paper_1706_02145_gb300 import binding as B
+    scene = synth.config2(0, N=args.N)
+    d = scene.incidents[0]
+    inc = B.make_incident("gaussian", waist=d.waist, focus=d.focus, alpha_G=d.alpha_G, n_beta=128)
+    ctx = B.celes_create(scene.positions, scene.radii, scene.n_sphere, scene.n0, scene.k0, scene.lmax,
+                         device=local_rank)
+    try:
+        B.celes_set_incident(ctx, [inc])
+        B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_MIXED)  # warm-up (and the tuner)
+        ic = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_MIXED)
+        bc = B.celes_get_coefficients(ctx)[0]
+        ir = B.celes_solve(ctx, REF_TOL, mode=B.CELES_SOLVE_MIXED, max_iter=40000, max_outer=40,
+                           raise_on_noconv=False)
+        br = B.celes_get_coefficients(ctx)[0]
+        ip = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_FP64, max_iter=20000, use_precond=False,
+                           raise_on_noconv=False)
+        bp = B.celes_get_coefficients(ctx)[0]
+    finally:
+        B.celes_destroy(ctx)
+    return {"N": scene.N, "lmax": scene.lmax,
+            "chosen": {"s": ic["seconds"], "iterations": ic["iterations"], "residual": ic["residual"],
+                       "error_vs_reference": rel_err(bc, br)},
+            "plain_fp64": {"s": ip["seconds"], "iterations": ip["iterations"], "residual": ip["residual"],
+                           "status": ip["status"], "error_vs_reference": rel_err(bp, br)},
+            "reference": {"tol": REF_TOL, "residual": ir["residual"], "iterations": ir["iterations"]},
+            "speedup": ip["seconds"] / ic["seconds"]}
+
+
 def max_over_ranks(x, dist, device):
     """The largest of a per-rank scalar (every rank gets it)."""
     if not dist:
@@ -1011,6 +1047,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.case:
         run_case(args)
+        return
+    if args.plain_full_only:
+        import torch
+        torch.cuda.set_device(local_rank)
+        from paper_1706_02145_gb300 import binding as B
+        B.load()
+        print(json.dumps({"plain_fp64_full": run_plain_full(args, local_rank)}), flush=True)
         return
     if args.c5:
         import torch
