@@ -67,11 +67,11 @@ typedef struct {
   int check_overlap;    /* reject overlapping spheres (default 1) */
   int chunks;           /* source chunks of the coupling kernel; 0 = automatic */
   int kernel;           /* celes_kernel: coupling-kernel variant (default AUTO) */
-  int autotune;         /* 1 (default): the first coupling product in each precision times the
-                           candidate launch shapes and source-chunk counts of the coupling kernel
-                           on this problem (cached per device, lmax, precision and size class) and
-                           keeps the fastest; it synchronises, so make that first product before
-                           any stream capture.  0: the built-in shape, about eight waves of chunks */
+  int autotune;         /* 1 (default): the first FP32 coupling product times the candidate launch
+                           shapes and source-chunk counts of the coupling kernel on this problem
+                           (cached per device, lmax and size class) and keeps the fastest; it
+                           synchronises, so make that first product before any stream capture.
+                           0 (and FP64 always): the built-in shape, about eight waves of chunks */
   int variant;          /* -1 (default): as autotune decides; 0..3 force the launch shape: bit 0 the
                            FP32 compile-time shape (0 = built-in, 1 = the alternative; FP64 always
                            uses the built-in one), bit 1 the cluster reduction of the partial sums

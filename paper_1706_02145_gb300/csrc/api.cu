@@ -397,7 +397,7 @@ int autotune(celes_ctx* c, int precision, const void* x, cudaStream_t st) {
     const size_t elem = precision == CELES_FP64 ? 16 : 8;
     const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
     // shapes: FP32 built-in / alternative, each without and with the
-    // cluster reduction of the partial sums; FP64 built-in with and without
+    // cluster reduction of the partial sums
     std::vector<int> vars = precision == CELES_FP64 ? std::vector<int>{0, 2} : std::vector<int>{0, 1, 2, 3};
     const double waves[3] = {4.0, 8.0, 16.0};
     int maxch = 1;
@@ -464,7 +464,9 @@ int coupling_apply(celes_ctx* c, const void* x, void* y, int nrhs, int precision
   const int pi = precision == CELES_FP64 ? 0 : 1;
   if (c->tune_chunks[pi] == 0) {
     const bool rtr = use_rtr(c, precision);
-    if (c->tune_variant[pi] < 0 && c->autotune && c->chunks_opt == 0 && rtr) {
+    // FP32 only: the FP64 kernel runs twice or so per solve (refinement
+    // residuals), too few launches to repay timing its candidates
+    if (c->tune_variant[pi] < 0 && c->autotune && c->chunks_opt == 0 && rtr && precision == CELES_FP32) {
       const int s = autotune(c, precision, x, st);
       if (s) return s;
     } else {
