@@ -539,16 +539,10 @@ __global__ void __launch_bounds__(256) precond_tri_inverse_kernel(const int64_t*
 }
 constexpr int kInvThreads = 256;
 
-// x = U^{-1} (L^{-1} (P y)) for one (block, RHS) per cluster of C CTAs.
-// The 32-row tiles are dealt zig-zag (tile t to CTA s when t mod 2C is s or
-// 2C - 1 - s), which evens out the triangular work of both products over the
-// CTAs.  A CTA takes its tiles one at a time with all its warps: each warp
-// sums a contiguous stretch of the tile rows' columns (one lane per row, so
-// a column of the tile is one coalesced 256-byte read, 16 reads in flight per
-// lane), the stretches are added in shared memory in a fixed order, and the
-// finished rows of t go into every CTA's copy of t.  One cluster barrier
-// separates the two products.  Every CTA gathers the whole (pivot-permuted)
-// block vector.
+// x = U^{-1} (L^{-1} (P y)) for one (block, RHS) per cluster of C CTAs; the
+// 32-row tiles are dealt round robin (warp w of CTA s takes tiles s + C (w +
+// 8 m)), one lane per row, so each column of a tile is one coalesced 256-byte
+// read.  Every CTA gathers the whole (pivot-permuted) block vector.
 template <typename R, typename F>
 __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const int64_t* __restrict__ block_off,
                                                                         const int64_t* __restrict__ mat_off, int nmax,
@@ -559,7 +553,6 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
                                                                         Pair2<R>* __restrict__ y) {
   using V = Pair2<F>;
   extern __shared__ __align__(16) unsigned char pi_smem[];
-  __shared__ V red[kInvThreads / 32][32];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int s = static_cast<int>(cluster.block_rank());
@@ -586,22 +579,17 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
   // every CTA of the cluster has started (and gathered) before any writes
   // into another's shared memory
   cluster.sync();
-  const int64_t period = 2LL * C;
-  auto mine = [&](int64_t t) {
-    const int64_t m = t % period;
-    return m == s || m == period - 1 - s;
-  };
-  // sum over columns [j0, j1) of A[i, j] v[j] (j1 <= j0: zero)
+  // row i: sum over columns [j0, j1) of A[i, j] v[j]
   auto rowdot = [&](int64_t i, int64_t j0, int64_t j1, const V* v) {
     F ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;
     const V* a = A + i;
     int64_t jj = j0;
-    for (; jj + 16 <= j1; jj += 16) {
-      V m[16];
+    for (; jj + 8 <= j1; jj += 8) {
+      V m[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) m[u] = a[(jj + u) * n];
+      for (int u = 0; u < 8; ++u) m[u] = a[(jj + u) * n];
 #pragma unroll
-      for (int u = 0; u < 16; u += 2) {
+      for (int u = 0; u < 8; u += 2) {
         const V v0 = v[jj + u], v1 = v[jj + u + 1];
         ar0 += m[u].re * v0.re - m[u].im * v0.im;
         ai0 += m[u].re * v0.im + m[u].im * v0.re;
@@ -616,49 +604,21 @@ __global__ void __launch_bounds__(kInvThreads) precond_apply_inv_kernel(const in
     }
     return V{ar0 + ar1, ai0 + ai1};
   };
-  // one tile's rows: warp w sums columns [c0 + w cs, c0 + (w + 1) cs) of [c0, c1)
-  // clipped to the row's own range, the warps' sums added in order
-  auto tile_rows = [&](int64_t tt, bool lower, const V* v) {
-    const int64_t i = tt * 32 + lane;
-    const int64_t c0 = lower ? 0 : tt * 32, c1 = lower ? tt * 32 + 32 : n;
-    const int64_t cs = ((c1 - c0 + NW - 1) / NW + 15) / 16 * 16;
-    const int64_t a0 = c0 + wid * cs, a1 = a0 + cs;
-    V part = V{0, 0};
-    if (i < n) {
-      const int64_t lo = lower ? a0 : (a0 > i ? a0 : i);
-      const int64_t hi = lower ? (a1 < i ? a1 : i) : (a1 < n ? a1 : n);
-      part = rowdot(i, lo, hi, v);
-    }
-    red[wid][lane] = part;
-    __syncthreads();
-    V sum = V{0, 0};
-    if (wid == 0) {
-#pragma unroll
-      for (int g = 0; g < NW; ++g) {
-        sum.re += red[g][lane].re;
-        sum.im += red[g][lane].im;
-      }
-    }
-    __syncthreads();
-    return sum;  // valid in warp 0
-  };
   // t = L^{-1} P y on own tiles (unit diagonal), into every CTA's copy of t
-  for (int64_t tt = 0; tt < T; ++tt) {
-    if (!mine(tt)) continue;
-    const V d = tile_rows(tt, true, xv);
+  for (int64_t tt = s + (int64_t)C * wid; tt < T; tt += (int64_t)C * NW) {
     const int64_t i = tt * 32 + lane;
-    if (wid == 0 && i < n) {
+    if (i < n) {
+      const V d = rowdot(i, 0, i, xv);
       const V t = V{xv[i].re + d.re, xv[i].im + d.im};
       for (int dst = 0; dst < C; ++dst) cluster.map_shared_rank(tv, dst)[i] = t;
     }
   }
   cluster.sync();
   // x = U^{-1} t on own tiles
-  for (int64_t tt = 0; tt < T; ++tt) {
-    if (!mine(tt)) continue;
-    const V o = tile_rows(tt, false, tv);
+  for (int64_t tt = s + (int64_t)C * wid; tt < T; tt += (int64_t)C * NW) {
     const int64_t i = tt * 32 + lane;
-    if (wid == 0 && i < n) {
+    if (i < n) {
+      const V o = rowdot(i, i, n, tv);
       const int64_t a = i / nmax;
       const int r = static_cast<int>(i - a * nmax);
       yr[(int64_t)perm[s0 + a] * nmax + r] = Pair2<R>{static_cast<R>(o.re), static_cast<R>(o.im)};
@@ -797,16 +757,7 @@ cudaError_t launch_apply_inv(int64_t nblocks, const int64_t* block_off, const in
         return se == cudaSuccess ? 1 : 0;
       }) == 0)
     return se != cudaSuccess ? se : cudaErrorInvalidConfiguration;
-  // CTAs per block: up to `csize`, but no more than keep every CTA of the
-  // launch resident at once (a partial second wave would double the time)
   const size_t smem = 2 * sizeof(Pair2<R>) * static_cast<size_t>(max_block_dim);
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, precond_apply_inv_kernel<R, R>, kInvThreads, smem) !=
-          cudaSuccess ||
-      occ < 1)
-    occ = 1;
-  const int64_t slots = static_cast<int64_t>(occ) * device_sms();
-  while (csize > 1 && nblocks * nrhs * csize > slots) --csize;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(nblocks * csize), static_cast<unsigned>(nrhs));
   cfg.blockDim = dim3(kInvThreads);
