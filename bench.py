@@ -84,7 +84,9 @@ def parse():
     ap.add_argument("--c5-edge", type=float, default=1000.0, help="--c5: preconditioner cuboid edge (nm)")
     ap.add_argument("--plain-full-only", action="store_true",
                     help="run only the uncapped plain FP64 solve of the bench workload beside the chosen form")
-    ap.add_argument("--case", choices=["coupling", "precond", "batch"], default=None,
+    ap.add_argument("--inner-tol", type=str, default="1e-5",
+                    help="--case solve: comma-separated inner tolerances of the mixed solve to compare")
+    ap.add_argument("--case", choices=["coupling", "precond", "batch", "solve"], default=None,
                     help="run one operation on a synthetic case and print its time (profiling); see run_case")
     ap.add_argument("--lmax", type=int, default=4, help="--case: degree")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="--case: precision")
@@ -1003,6 +1005,22 @@ def run_case(args):
         B.celes_batch_destroy(bt)
         for c in ctxs:
             B.celes_destroy(c)
+        return
+    if args.case == "solve":
+        # the mixed solve of the bench workload (--N spheres, --lmax) to 1e-6
+        # for each inner tolerance: time, iterations and FP64 matvecs
+        sc = synth.config2(0, N=args.N, lmax=args.lmax)
+        d = sc.incidents[0]
+        ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax)
+        B.celes_set_incident(ctx, [B.make_incident("gaussian", waist=d.waist, focus=d.focus, alpha_G=d.alpha_G,
+                                                   n_beta=128)])
+        B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_MIXED)  # warm-up (and the tuner)
+        for it in [float(v) for v in args.inner_tol.split(",")]:
+            info = B.celes_solve(ctx, TOL, mode=B.CELES_SOLVE_MIXED, inner_tol=it, raise_on_noconv=False)
+            print(f"N={sc.N} lmax={sc.lmax} mixed solve to {TOL:g}, inner tol {it:g}: {info['seconds']:.3f} s, "
+                  f"{info['iterations']} iterations, {info['matvecs_fp32']} FP32 and {info['matvecs_fp64']} FP64 "
+                  f"matvecs, residual {info['residual']:.3e}, status {info['status']}")
+        B.celes_destroy(ctx)
         return
     kern = {"auto": B.CELES_KERNEL_AUTO, "direct": B.CELES_KERNEL_DIRECT, "rtr": B.CELES_KERNEL_RTR}[args.kernel]
     sc = synth.config2(0, N=args.N, lmax=args.lmax) if args.recipe == "slab" else synth.config5(0)
