@@ -35,31 +35,9 @@ template <int L, typename R>
 constexpr bool kPacked = std::is_same<R, float>::value && L <= 4;
 // launch-shape option bits of the pair code: 1 = the x+ phase multiply on the
 // packed FMA, 2 = packed rotations at every lmax (lmax 5 with x' and y' in
-// shared memory has the registers for them), 4 = the forward rotation's
-// Wigner-d values kept in shared memory for the backward one (they are built
-// once per pair instead of twice, on the scalar FMA half that limits the
-// kernel)
+// shared memory has the registers for them)
 template <int L, typename R, int OPT>
 constexpr bool kPackedRot = std::is_same<R, float>::value && (L <= 4 || (OPT & 2) != 0);
-
-// first slot of degree l's canonical Wigner-d values in the per-thread store
-template <int l>
-struct DvOff {
-  static constexpr int v = DvOff<l - 1>::v + DCount<l - 1>::ncanon;
-};
-template <>
-struct DvOff<1> {
-  static constexpr int v = 0;
-};
-
-// per-thread column of a shared-memory array [slots][BLOCK] (stride BLOCK);
-// a null view when the option is off
-template <typename R, int BLOCK>
-struct DvSmem {
-  R* a;
-  __device__ __forceinline__ R& operator()(int q) const { return a[q * BLOCK]; }
-};
-struct DvNone {};
 
 template <typename R>
 struct alignas(4 * sizeof(R)) Quad4 {
@@ -366,16 +344,12 @@ __device__ __forceinline__ void rot_fwd_row(const R* dv, const R (&xt)[2][2 * l 
 // two-lane FMA, which moves work from the scalar half of the FP32 lanes (that
 // carries the axial entries, the axial apply and the phases) to the half that
 // carries the packed rotations; an autotuner candidate (ConfigAlt at lmax 4)
-template <int L, int l, int OPT, typename R, typename XV, typename DV, int... MUI>
+template <int L, int l, int OPT, typename R, typename XV, int... MUI>
 __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
-                                              const DV& dvs, std::integer_sequence<int, MUI...>) {
+                                              std::integer_sequence<int, MUI...>) {
   constexpr int NH = L * (L + 2);
   R dv[DCount<l>::ncanon];
   dmatrix<L, l>(g, dv);
-  if constexpr ((OPT & 4) != 0) {
-#pragma unroll
-    for (int c = 0; c < DCount<l>::ncanon; ++c) dvs(DvOff<l>::v + c) = dv[c];
-  }
   R xt[2][2 * l + 1][2];
 #pragma unroll
   for (int mi = 0; mi <= 2 * l; ++mi) {
@@ -400,10 +374,10 @@ __device__ __forceinline__ void rot_fwd_block(const Geom<L, R>& g, const Pair2<R
   (rot_fwd_row<L, l, MUI - l, OPT>(dv, xt, xp, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
 }
 
-template <int L, int OPT, typename R, typename XV, typename DV, int... LI>
-__device__ __forceinline__ void rot_fwd(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, const DV& dvs,
+template <int L, int OPT, typename R, typename XV, int... LI>
+__device__ __forceinline__ void rot_fwd(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp,
                                         std::integer_sequence<int, LI...>) {
-  (rot_fwd_block<L, LI + 1, OPT>(g, xs, xp, dvs, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+  (rot_fwd_block<L, LI + 1, OPT>(g, xs, xp, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
 }
 
 // ---- step 3: axial translation --------------------------------------------
@@ -632,23 +606,17 @@ __device__ __forceinline__ void rot_bwd_col(const Geom<L, R>& g, const R* dv, YV
   (void)NH;
 }
 
-template <int L, int l, int OPT, typename R, typename YV, typename Acc, typename DV, int... MI>
-__device__ __forceinline__ void rot_bwd_block(const Geom<L, R>& g, YV& yp, Acc& acc, const DV& dvs,
+template <int L, int l, int OPT, typename R, typename YV, typename Acc, int... MI>
+__device__ __forceinline__ void rot_bwd_block(const Geom<L, R>& g, YV& yp, Acc& acc,
                                               std::integer_sequence<int, MI...>) {
   R dv[DCount<l>::ncanon];
-  if constexpr ((OPT & 4) != 0) {
-#pragma unroll
-    for (int c = 0; c < DCount<l>::ncanon; ++c) dv[c] = dvs(DvOff<l>::v + c);
-  } else {
-    dmatrix<L, l>(g, dv);
-  }
+  dmatrix<L, l>(g, dv);
   (rot_bwd_col<L, l, MI - l, OPT>(g, dv, yp, acc, std::make_integer_sequence<int, 2 * l + 1>{}), ...);
 }
 
-template <int L, int OPT, typename R, typename YV, typename Acc, typename DV, int... LI>
-__device__ __forceinline__ void rot_bwd(const Geom<L, R>& g, YV& yp, Acc& acc, const DV& dvs,
-                                        std::integer_sequence<int, LI...>) {
-  (rot_bwd_block<L, LI + 1, OPT>(g, yp, acc, dvs, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
+template <int L, int OPT, typename R, typename YV, typename Acc, int... LI>
+__device__ __forceinline__ void rot_bwd(const Geom<L, R>& g, YV& yp, Acc& acc, std::integer_sequence<int, LI...>) {
+  (rot_bwd_block<L, LI + 1, OPT>(g, yp, acc, std::make_integer_sequence<int, 2 * (LI + 1) + 1>{}), ...);
 }
 
 // storage views: registers (compile-time index) or a per-thread column of a
@@ -696,13 +664,11 @@ struct RowAccSmem {
   __device__ __forceinline__ void store(int r, const R (&c)[4]) const { a[r * BLOCK] = Quad4<R>{c[0], c[1], c[2], c[3]}; }
 };
 
-template <int L, bool INPLACE, bool SYM, typename R, int OPT = 0, typename XV, typename YV, typename Acc,
-          typename DV = DvNone>
-__device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, YV& yp, Acc& acc,
-                                     const DV& dvs = DV{}) {
-  rot_fwd<L, OPT>(g, xs, xp, dvs, std::make_integer_sequence<int, L>{});
+template <int L, bool INPLACE, bool SYM, typename R, int OPT = 0, typename XV, typename YV, typename Acc>
+__device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __restrict__ xs, XV& xp, YV& yp, Acc& acc) {
+  rot_fwd<L, OPT>(g, xs, xp, std::make_integer_sequence<int, L>{});
   axial<L, INPLACE, SYM>(g, xp, yp, std::make_integer_sequence<int, L + 1>{});
-  rot_bwd<L, OPT>(g, yp, acc, dvs, std::make_integer_sequence<int, L>{});
+  rot_bwd<L, OPT>(g, yp, acc, std::make_integer_sequence<int, L>{});
 }
 
 // One pair with the tables rebuilt per stage from the pair's scalars: the
@@ -710,14 +676,13 @@ __device__ __forceinline__ void pair(const Geom<L, R>& g, const Pair2<R>* __rest
 // step.  The rebuild before the backward rotation reads the scalars through
 // an optimizer barrier, so the compiler cannot keep the forward rotation's
 // tables alive across the axial step (fewer live registers per thread).
-template <int L, bool INPLACE, bool SYM, int OPT = 0, typename XV, typename YV, typename Acc,
-          typename DV = DvNone>
+template <int L, bool INPLACE, bool SYM, int OPT = 0, typename XV, typename YV, typename Acc>
 __device__ __forceinline__ void pair_lazy(const GeomS& q, const Pair2<float>* __restrict__ xs, XV& xp, YV& yp,
-                                          Acc& acc, const DV& dvs = DV{}) {
+                                          Acc& acc) {
   {
     Geom<L, float> g;
     geometry_angles<L>(q.ct, q.st, q.cph, q.sph, g);
-    rot_fwd<L, OPT>(g, xs, xp, dvs, std::make_integer_sequence<int, L>{});
+    rot_fwd<L, OPT>(g, xs, xp, std::make_integer_sequence<int, L>{});
   }
   {
     Geom<L, float> g;
@@ -729,7 +694,7 @@ __device__ __forceinline__ void pair_lazy(const GeomS& q, const Pair2<float>* __
   {
     Geom<L, float> g;
     geometry_angles<L>(ct, st, cph, sph, g);
-    rot_bwd<L, OPT>(g, yp, acc, dvs, std::make_integer_sequence<int, L>{});
+    rot_bwd<L, OPT>(g, yp, acc, std::make_integer_sequence<int, L>{});
   }
 }
 
@@ -755,15 +720,15 @@ struct Config {
 
 // The alternative FP32 launch shape of each lmax, the second candidate of
 // the autotuner (celes_ctx tuning): lmax 1-2 64-receiver CTAs, lmax 3 the
-// register allocator left free (two CTAs per SM), lmax 4 the Wigner-d values
-// kept in shared memory between the two rotations, lmax 5 64-receiver CTAs
-// with x' and y' in shared memory (in place) and the rotations on the packed
-// FMA.  Everything else as in Config.
+// register allocator left free (two CTAs per SM), lmax 4 the x+ phase
+// multiply on the packed FMA, lmax 5 64-receiver CTAs with x' and y' in shared
+// memory (in place) and the rotations on the packed FMA.  Everything else as
+// in Config.
 template <int L, typename R>
 struct ConfigAlt : Config<L, R> {
   static constexpr int BLOCK = (L <= 2 || L == 5) ? 64 : 128;
   static constexpr int MINB = 1;
-  static constexpr int OPT = L == 4 ? 4 : (L == 5 ? 2 : 0);
+  static constexpr int OPT = L == 4 ? 1 : (L == 5 ? 2 : 0);
   static constexpr bool XY_SMEM = Config<L, R>::XY_SMEM || L == 5;
   static constexpr bool XY_INPLACE = XY_SMEM;
 };
@@ -776,9 +741,7 @@ struct Layout {
   static constexpr size_t off_x = off_pos + sizeof(Pos4) * C::TJ;
   static constexpr size_t off_acc = off_x + sizeof(Pair2<R>) * 2 * NH * C::TJ;
   static constexpr size_t off_xy = off_acc + (C::ACC_SMEM ? col : 0);
-  static constexpr size_t off_dv = off_xy + (C::XY_SMEM ? (C::XY_INPLACE ? 1 : 2) * col : 0);
-  static constexpr int dv_slots = DvOff<L>::v + DCount<L>::ncanon;
-  static constexpr size_t bytes = off_dv + ((C::OPT & 4) ? sizeof(R) * dv_slots * C::BLOCK : 0);
+  static constexpr size_t bytes = off_xy + (C::XY_SMEM ? (C::XY_INPLACE ? 1 : 2) * col : 0);
 };
 
 // One tile: receivers rb*BLOCK .. +BLOCK against sources j0 .. j1 - 1; writes
@@ -856,15 +819,14 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
         const Pair2<R>* xs = sx + jj * 2 * NH;
         auto run = [&](auto& xp, auto& yp) {
           constexpr bool INPL = C::XY_SMEM && C::XY_INPLACE;
-          const DvSmem<R, BLOCK> dvs{reinterpret_cast<R*>(smem_raw + LY::off_dv) + tid};
           if constexpr (C::ACC_SMEM) {
             RowAccSmem<R, BLOCK> acc{sacc4 + tid};
-            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL, C::OPT>(gs, xs, xp, yp, acc, dvs);
-            else pair<L, INPL, C::SYM_AXIAL, R, C::OPT>(g, xs, xp, yp, acc, dvs);
+            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL, C::OPT>(gs, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R, C::OPT>(g, xs, xp, yp, acc);
           } else {
             RowAccReg<R> acc{areg};
-            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL, C::OPT>(gs, xs, xp, yp, acc, dvs);
-            else pair<L, INPL, C::SYM_AXIAL, R, C::OPT>(g, xs, xp, yp, acc, dvs);
+            if constexpr (LAZY) pair_lazy<L, INPL, C::SYM_AXIAL, C::OPT>(gs, xs, xp, yp, acc);
+            else pair<L, INPL, C::SYM_AXIAL, R, C::OPT>(g, xs, xp, yp, acc);
           }
         };
         if constexpr (C::XY_SMEM) {
