@@ -97,7 +97,10 @@ def parse():
                          "monodisperse slab (lmax 3)")
     ap.add_argument("--edge", type=float, default=900.0, help="--case precond: cuboid edge (nm)")
     ap.add_argument("--autotune", type=int, default=1, help="--case coupling: 1 = tune the launch shape, 0 = built-in")
-    ap.add_argument("--variant", type=int, default=-1, help="--case coupling: force the FP32 launch shape (0 or 1)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="--case coupling: force the FP32 launch shape (0-7: bit 0 the alternative shape, bit 1 the "
+                         "cluster reduction, bit 2 the reduction in L2)")
+    ap.add_argument("--chunks", type=int, default=0, help="--case coupling: source chunks (0: automatic)")
     ap.add_argument("--ensembles", type=int, default=12, help="--case batch: ensembles")
     ap.add_argument("--rhs", type=int, default=0,
                     help="--case: right-hand sides (0 = 1 for coupling, 4 plane waves per ensemble for batch)")
@@ -177,14 +180,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key):
+def ncu_traffic(kernel_key, shape=None):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when it is absent or was taken on other kernel source."""
+    None when it is absent, was taken on other kernel source, or on another
+    launch shape (variant, chunks) than `shape`."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(kernel_key)
+        if shape is not None and e and (e.get("variant"), e.get("chunks")) != tuple(shape):
+            return None
         if e and e.get("source_hash") == kernel_source_hash():
             return e.get("dram_bytes_per_launch")
     except Exception:
@@ -785,7 +791,8 @@ def run_ours(args, rank, world, local_rank):
     dom = "coupling_fp32" if k32_ms >= k64_ms else "coupling_fp64"
     peak = peaks["fp32_tflops"] if dom == "coupling_fp32" else peaks["fp64_tflops"]
     ach = kernels[dom]["tflops"]
-    traffic = ncu_traffic(f"{dom}_L{L}")
+    shp = kernels[dom].get("shape")
+    traffic = ncu_traffic(f"{dom}_L{L}", (shp["variant"], shp["chunks"]) if shp else None)
     derived = peaks["sms"] * 128 * 2 * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": dom,
@@ -1025,7 +1032,7 @@ def run_case(args):
     kern = {"auto": B.CELES_KERNEL_AUTO, "direct": B.CELES_KERNEL_DIRECT, "rtr": B.CELES_KERNEL_RTR}[args.kernel]
     sc = synth.config2(0, N=args.N, lmax=args.lmax) if args.recipe == "slab" else synth.config5(0)
     ctx = B.celes_create(sc.positions, sc.radii, sc.n_sphere, sc.n0, sc.k0, sc.lmax, kernel=kern,
-                         autotune=bool(args.autotune), variant=args.variant)
+                         autotune=bool(args.autotune), variant=args.variant, chunks=args.chunks)
     nrhs = max(1, args.rhs) if args.case == "coupling" else 1
     x = torch.randn(nrhs, sc.N, sc.nmax, dtype=dt, device="cuda", generator=g)
     y = torch.empty_like(x)

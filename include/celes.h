@@ -72,10 +72,14 @@ typedef struct {
                            (cached per device, lmax and size class) and keeps the fastest; it
                            synchronises, so make that first product before any stream capture.
                            0 (and FP64 always): the built-in shape, about eight waves of chunks */
-  int variant;          /* -1 (default): as autotune decides; 0..3 force the launch shape: bit 0 the
+  int variant;          /* -1 (default): as autotune decides; 0..7 force the launch shape: bit 0 the
                            FP32 compile-time shape (0 = built-in, 1 = the alternative; FP64 always
                            uses the built-in one), bit 1 the cluster reduction of the partial sums
-                           (thread-block clusters of up to 8 source chunks) */
+                           (thread-block clusters of up to 8 source chunks), bit 2 (FP32 only) the
+                           partial sums of all chunks added into one slice by vector reductions in
+                           L2, so that only the final sums reach DRAM; with bit 2 the summation
+                           order, and so the last bits of an FP32 product, vary between calls.
+                           Values above 7 give CELES_EINVAL */
 } celes_options;
 
 typedef enum { CELES_PLANE_WAVE = 0, CELES_GAUSSIAN_BEAM = 1 } celes_incident_kind;
@@ -173,7 +177,8 @@ int celes_precond_build(celes_ctx* ctx, double cuboid_edge);
 
 /* Launch shape the context's coupling kernel uses in `precision`: variant
  * (bit 0: alternative FP32 shape; bit 1: cluster reduction of the partial
- * sums, see celes_options.variant), source chunks per product and, if
+ * sums; bit 2: reduction in L2, see celes_options.variant), source chunks
+ * per product and, if
  * the autotuner chose it, the timed duration of the winning candidate (ms; 0
  * otherwise).  CELES_ESTATE before the first coupling product in that
  * precision.  Measurement support; the paper has no counterpart. */

@@ -34,17 +34,18 @@ namespace celes {
                                             void* partial, double k, int chunks, cudaStream_t st);         \
   int coupling_rpb_##LL(int precision);                                                                    \
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
-                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl);   \
+                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl,    \
+                                       int atomic);                                                        \
   int coupling_rtr_rpb_##LL(int precision);                                                                \
-  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl);                                      \
+  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl, int atomic);                          \
   int coupling_rtr_slots_##LL(int precision);                                                              \
   long long coupling_rtr_flops_##LL();                                                                     \
   int coupling_terms_export_##LL(int* idx, double* val, int cap);
 #define CELES_DECLARE_ALT(LL)                                                                              \
   cudaError_t launch_coupling_rtr_alt_##LL(int64_t N, const void* pos, const void* x, void* partial,       \
-                                           double k, int chunks, cudaStream_t st, int maxcl);              \
+                                           double k, int chunks, cudaStream_t st, int maxcl, int atomic);  \
   int coupling_rtr_alt_rpb_##LL();                                                                         \
-  int coupling_rtr_alt_slices_##LL(int chunks, int maxcl);                                                 \
+  int coupling_rtr_alt_slices_##LL(int chunks, int maxcl, int atomic);                                     \
   int coupling_rtr_alt_slots_##LL();
 CELES_DECLARE_ALT(1)
 CELES_DECLARE_ALT(2)
@@ -71,13 +72,13 @@ cudaError_t launch_coupling_partial(int L, int precision, int64_t N, const void*
   }
 }
 cudaError_t launch_coupling_rtr(int L, int precision, int64_t N, const void* pos, const void* x, void* partial,
-                                double k, int chunks, cudaStream_t st, int maxcl = 1) {
+                                double k, int chunks, cudaStream_t st, int maxcl = 1, int atomic = 0) {
   switch (L) {
-    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st, maxcl);
-    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st, maxcl);
-    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st, maxcl);
-    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st, maxcl);
-    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st, maxcl);
+    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st, maxcl, atomic);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -86,18 +87,20 @@ int coupling_rtr_slots(int L, int precision);
 
 // launch shape `variant`: bit 0 the compile-time shape (0: Config, 1:
 // ConfigAlt, FP32 only), bit 1 the cluster reduction of the partial sums
-// (clusters of up to 8 chunks)
+// (clusters of up to 8 chunks), bit 2 the in-L2 vector reduction of all
+// chunks into one slice (FP32 only)
 cudaError_t launch_coupling_rtr_v(int L, int precision, int variant, int64_t N, const void* pos, const void* x,
                                   void* partial, double k, int chunks, cudaStream_t st) {
   const int maxcl = (variant & 2) ? 8 : 1;
+  const int atomic = (variant & 4) && precision == CELES_FP32 ? 1 : 0;
   if ((variant & 1) == 0 || precision == CELES_FP64)
-    return launch_coupling_rtr(L, precision, N, pos, x, partial, k, chunks, st, maxcl);
+    return launch_coupling_rtr(L, precision, N, pos, x, partial, k, chunks, st, maxcl, atomic);
   switch (L) {
-    case 1: return launch_coupling_rtr_alt_1(N, pos, x, partial, k, chunks, st, maxcl);
-    case 2: return launch_coupling_rtr_alt_2(N, pos, x, partial, k, chunks, st, maxcl);
-    case 3: return launch_coupling_rtr_alt_3(N, pos, x, partial, k, chunks, st, maxcl);
-    case 4: return launch_coupling_rtr_alt_4(N, pos, x, partial, k, chunks, st, maxcl);
-    case 5: return launch_coupling_rtr_alt_5(N, pos, x, partial, k, chunks, st, maxcl);
+    case 1: return launch_coupling_rtr_alt_1(N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 2: return launch_coupling_rtr_alt_2(N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 3: return launch_coupling_rtr_alt_3(N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 4: return launch_coupling_rtr_alt_4(N, pos, x, partial, k, chunks, st, maxcl, atomic);
+    case 5: return launch_coupling_rtr_alt_5(N, pos, x, partial, k, chunks, st, maxcl, atomic);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -116,22 +119,23 @@ int coupling_rtr_rpb_v(int L, int precision, int variant) {
 // cluster reduction of the shared-memory accumulator shapes divides it)
 int coupling_rtr_slices_v(int L, int precision, int variant, int chunks) {
   const int maxcl = (variant & 2) ? 8 : 1;
+  const int atomic = (variant & 4) && precision == CELES_FP32 ? 1 : 0;
   if ((variant & 1) == 0 || precision == CELES_FP64) {
     switch (L) {
-      case 1: return coupling_rtr_slices_1(precision, chunks, maxcl);
-      case 2: return coupling_rtr_slices_2(precision, chunks, maxcl);
-      case 3: return coupling_rtr_slices_3(precision, chunks, maxcl);
-      case 4: return coupling_rtr_slices_4(precision, chunks, maxcl);
-      case 5: return coupling_rtr_slices_5(precision, chunks, maxcl);
+      case 1: return coupling_rtr_slices_1(precision, chunks, maxcl, atomic);
+      case 2: return coupling_rtr_slices_2(precision, chunks, maxcl, atomic);
+      case 3: return coupling_rtr_slices_3(precision, chunks, maxcl, atomic);
+      case 4: return coupling_rtr_slices_4(precision, chunks, maxcl, atomic);
+      case 5: return coupling_rtr_slices_5(precision, chunks, maxcl, atomic);
       default: return chunks;
     }
   }
   switch (L) {
-    case 1: return coupling_rtr_alt_slices_1(chunks, maxcl);
-    case 2: return coupling_rtr_alt_slices_2(chunks, maxcl);
-    case 3: return coupling_rtr_alt_slices_3(chunks, maxcl);
-    case 4: return coupling_rtr_alt_slices_4(chunks, maxcl);
-    case 5: return coupling_rtr_alt_slices_5(chunks, maxcl);
+    case 1: return coupling_rtr_alt_slices_1(chunks, maxcl, atomic);
+    case 2: return coupling_rtr_alt_slices_2(chunks, maxcl, atomic);
+    case 3: return coupling_rtr_alt_slices_3(chunks, maxcl, atomic);
+    case 4: return coupling_rtr_alt_slices_4(chunks, maxcl, atomic);
+    case 5: return coupling_rtr_alt_slices_5(chunks, maxcl, atomic);
     default: return chunks;
   }
 }
@@ -396,9 +400,10 @@ int autotune(celes_ctx* c, int precision, const void* x, cudaStream_t st) {
   if (!have) {
     const size_t elem = precision == CELES_FP64 ? 16 : 8;
     const size_t per = static_cast<size_t>(c->N) * c->nmax * elem;
-    // shapes: FP32 built-in / alternative, each without and with the
-    // cluster reduction of the partial sums
-    std::vector<int> vars = precision == CELES_FP64 ? std::vector<int>{0, 2} : std::vector<int>{0, 1, 2, 3};
+    // shapes: FP32 built-in / alternative, each with the partial sums in
+    // slices, added in clusters, added in L2, or both
+    std::vector<int> vars =
+        precision == CELES_FP64 ? std::vector<int>{0, 2} : std::vector<int>{0, 1, 2, 3, 4, 5, 6, 7};
     const double waves[3] = {4.0, 8.0, 16.0};
     int maxch = 1;
     for (int v : vars)
@@ -565,7 +570,7 @@ extern "C" int celes_create(celes_ctx** out, int64_t N, const double* positions,
   c->autotune = opt ? opt->autotune : 1;
   if (opt && opt->variant >= 0) {
     // a forced launch shape (tests and measurements); the chunks as usual
-    if (opt->variant > 3) return CELES_EINVAL;
+    if (opt->variant > 7) return CELES_EINVAL;
     c->tune_variant[0] = opt->variant & 2;
     c->tune_variant[1] = opt->variant;
   }

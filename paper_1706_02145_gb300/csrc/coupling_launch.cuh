@@ -118,13 +118,13 @@ long long rtr_flops_per_pair_t() {
 // the alternative FP32 shape (ConfigAlt), in a translation unit of its own
 #define CELES_INSTANTIATE_RTR_ALT(LL)                                                                      \
   cudaError_t launch_coupling_rtr_alt_##LL(int64_t N, const void* pos, const void* x, void* partial,       \
-                                           double k, int chunks, cudaStream_t st, int maxcl) {             \
+                                           double k, int chunks, cudaStream_t st, int maxcl, int atomic) { \
     return rtr::launch_partial<LL, float, rtr::ConfigAlt<LL, float>>(N, pos, x, partial, k, chunks, st,    \
-                                                                     maxcl);                               \
+                                                                     maxcl, atomic != 0);                  \
   }                                                                                                         \
   int coupling_rtr_alt_rpb_##LL() { return rtr::ConfigAlt<LL, float>::BLOCK; }                             \
-  int coupling_rtr_alt_slices_##LL(int chunks, int maxcl) {                                                \
-    return chunks / rtr::partial_cluster<LL, float, rtr::ConfigAlt<LL, float>>(chunks, maxcl);             \
+  int coupling_rtr_alt_slices_##LL(int chunks, int maxcl, int atomic) {                                    \
+    return rtr::partial_slices<LL, float, rtr::ConfigAlt<LL, float>>(chunks, maxcl, atomic != 0);          \
   }                                                                                                         \
   int coupling_rtr_alt_slots_##LL() { return rtr::resident_slots<LL, float, rtr::ConfigAlt<LL, float>>(); }
 
@@ -140,16 +140,18 @@ long long rtr_flops_per_pair_t() {
     return launch_coupling_partial_t<LL, float>(N, pos, x, partial, k, chunks, st);                        \
   }                                                                                                        \
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
-                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl) {  \
-    return precision == 0 ? rtr::launch_partial<LL, double>(N, pos, x, partial, k, chunks, st, maxcl)      \
-                          : rtr::launch_partial<LL, float>(N, pos, x, partial, k, chunks, st, maxcl);      \
+                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl,    \
+                                       int atomic) {                                                       \
+    return precision == 0                                                                                  \
+               ? rtr::launch_partial<LL, double>(N, pos, x, partial, k, chunks, st, maxcl, false)          \
+               : rtr::launch_partial<LL, float>(N, pos, x, partial, k, chunks, st, maxcl, atomic != 0);    \
   }                                                                                                        \
   int coupling_rtr_rpb_##LL(int precision) {                                                               \
     return precision == 0 ? rtr::Config<LL, double>::BLOCK : rtr::Config<LL, float>::BLOCK;               \
   }                                                                                                        \
-  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl) {                                     \
-    return chunks / (precision == 0 ? rtr::partial_cluster<LL, double>(chunks, maxcl)                      \
-                                    : rtr::partial_cluster<LL, float>(chunks, maxcl));                     \
+  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl, int atomic) {                         \
+    return precision == 0 ? rtr::partial_slices<LL, double>(chunks, maxcl, false)                          \
+                          : rtr::partial_slices<LL, float>(chunks, maxcl, atomic != 0);                    \
   }                                                                                                        \
   int coupling_rpb_##LL(int precision) {                                                                   \
     if (precision == 0) return (FP64_UNROLLED) ? CouplingLayout<LL, double>::RPB : kGenericRPB;           \

@@ -22,9 +22,10 @@
 namespace celes {
 #define CELES_DECLARE_RTR(LL)                                                                               \
   cudaError_t launch_coupling_rtr_##LL(int precision, int64_t N, const void* pos, const void* x,           \
-                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl);   \
+                                       void* partial, double k, int chunks, cudaStream_t st, int maxcl,    \
+                                       int atomic);                                                        \
   int coupling_rtr_rpb_##LL(int precision);                                                                \
-  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl);                                      \
+  int coupling_rtr_slices_##LL(int precision, int chunks, int maxcl, int atomic);                          \
   int coupling_rtr_slots_##LL(int precision);
 CELES_DECLARE_RTR(1)
 CELES_DECLARE_RTR(2)
@@ -68,11 +69,11 @@ cudaError_t launch_rtr(int L, int precision, int64_t N, const void* pos, const v
                        int chunks, cudaStream_t st) {
   using namespace celes;
   switch (L) {
-    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st, 1);
-    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st, 1);
-    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st, 1);
-    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st, 1);
-    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st, 1);
+    case 1: return launch_coupling_rtr_1(precision, N, pos, x, partial, k, chunks, st, 1, 0);
+    case 2: return launch_coupling_rtr_2(precision, N, pos, x, partial, k, chunks, st, 1, 0);
+    case 3: return launch_coupling_rtr_3(precision, N, pos, x, partial, k, chunks, st, 1, 0);
+    case 4: return launch_coupling_rtr_4(precision, N, pos, x, partial, k, chunks, st, 1, 0);
+    case 5: return launch_coupling_rtr_5(precision, N, pos, x, partial, k, chunks, st, 1, 0);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -92,11 +93,11 @@ int rtr_slots(int L, int precision) {
 int rtr_slices(int L, int precision, int chunks) {
   using namespace celes;
   switch (L) {
-    case 1: return coupling_rtr_slices_1(precision, chunks, 1);
-    case 2: return coupling_rtr_slices_2(precision, chunks, 1);
-    case 3: return coupling_rtr_slices_3(precision, chunks, 1);
-    case 4: return coupling_rtr_slices_4(precision, chunks, 1);
-    case 5: return coupling_rtr_slices_5(precision, chunks, 1);
+    case 1: return coupling_rtr_slices_1(precision, chunks, 1, 0);
+    case 2: return coupling_rtr_slices_2(precision, chunks, 1, 0);
+    case 3: return coupling_rtr_slices_3(precision, chunks, 1, 0);
+    case 4: return coupling_rtr_slices_4(precision, chunks, 1, 0);
+    case 5: return coupling_rtr_slices_5(precision, chunks, 1, 0);
     default: return chunks;
   }
 }

@@ -751,7 +751,11 @@ struct Layout {
 // cluster (one receiver block, consecutive source chunks) add their sums
 // through distributed shared memory and write one partial per cluster, so
 // the partial-sum traffic shrinks by the cluster size.
-template <int L, typename R, typename C, bool CRED = false>
+// ATOM (FP32): the sums are added into out with vector reductions in L2
+// (out zeroed before the launch), so all source chunks share one slice and
+// only the final sums reach DRAM; the order of the additions, and so the
+// last bits of the result, vary from launch to launch.
+template <int L, typename R, typename C, bool CRED = false, bool ATOM = false>
 __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
                                          Pair2<R>* __restrict__ outp, double k, int rb, int j0, int j1,
                                          unsigned char* smem_raw) {
@@ -861,11 +865,60 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
           a2 += v.z;
           a3 += v.w;
         }
-        out[r] = Pair2<R>{a0, a1};
-        out[NH + r] = Pair2<R>{a2, a3};
+        if constexpr (ATOM) {
+          atomicAdd(reinterpret_cast<float2*>(out + r), make_float2(a0, a1));
+          atomicAdd(reinterpret_cast<float2*>(out + NH + r), make_float2(a2, a3));
+        } else {
+          out[r] = Pair2<R>{a0, a1};
+          out[NH + r] = Pair2<R>{a2, a3};
+        }
       }
     }
     cl.sync();  // no CTA leaves while others read its shared memory
+    return;
+  }
+  if constexpr (ATOM) {
+    static_assert(sizeof(R) == 4, "vector reductions of the partial sums are FP32 only");
+    // the 2 NH complex sums of a receiver are NH float4 (element pairs 2p,
+    // 2p+1 of the flattened [2][NH] row: the + rows, then the - rows)
+    auto elem = [&](int t, int e, float& re, float& im) {
+      const int r = e < NH ? e : e - NH;
+      if constexpr (C::ACC_SMEM) {
+        const Quad4<R> v = sacc4[r * BLOCK + t];
+        re = e < NH ? v.x : v.z;
+        im = e < NH ? v.y : v.w;
+      } else {
+        re = areg[4 * r + (e < NH ? 0 : 2)];
+        im = areg[4 * r + (e < NH ? 1 : 3)];
+      }
+    };
+    if constexpr (C::ACC_SMEM) {
+      // a warp's 32 receivers are contiguous in out: lane-consecutive float4
+      // (512 B per warp instruction); each thread's sums are written by its
+      // own thread only, so the warp's accumulators are complete here
+      __syncwarp();
+      const int w0 = tid & ~31;
+      const int lane = tid & 31;
+      float4* base = reinterpret_cast<float4*>(outp + (size_t)(rb * BLOCK + w0) * (2 * NH));
+      for (int q = lane; q < 32 * NH; q += 32) {
+        const int t = q / NH;
+        const int p = q - t * NH;
+        if (rb * BLOCK + w0 + t >= N) break;  // q ascending: later q are further receivers
+        float4 v;
+        elem(w0 + t, 2 * p, v.x, v.y);
+        elem(w0 + t, 2 * p + 1, v.z, v.w);
+        atomicAdd(base + q, v);
+      }
+    } else if (active) {
+      float4* base = reinterpret_cast<float4*>(outp + (size_t)i * (2 * NH));
+#pragma unroll
+      for (int p = 0; p < NH; ++p) {
+        float4 v;
+        elem(tid, 2 * p, v.x, v.y);
+        elem(tid, 2 * p + 1, v.z, v.w);
+        atomicAdd(base + p, v);
+      }
+    }
     return;
   }
   if (active) {
@@ -891,7 +944,8 @@ __device__ __forceinline__ void rtr_tile(int N, const Pos4* __restrict__ pos, co
 // +- basis, [chunks][N][2][NH] complex (same layout as the direct kernel)
 // CRED: launched with clusters of `ncl` CTAs along y; cluster c writes
 // partial slice c (the grid's y extent is a multiple of ncl)
-template <int L, typename R, typename C = Config<L, R>, bool CRED = false>
+// ATOM: every tile adds into slice 0 (zeroed before the launch)
+template <int L, typename R, typename C = Config<L, R>, bool CRED = false, bool ATOM = false>
 __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     rtr_partial_kernel(int N, const Pos4* __restrict__ pos, const Pair2<R>* __restrict__ x,
                        Pair2<R>* __restrict__ partial, double k, int chunk, int ncl) {
@@ -899,8 +953,9 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
   constexpr int NH = L * (L + 2);
   const int j0 = blockIdx.y * chunk;
   const int j1 = min(N, j0 + chunk);
-  const int slice = CRED ? static_cast<int>(blockIdx.y) / ncl : static_cast<int>(blockIdx.y);
-  rtr_tile<L, R, C, CRED>(N, pos, x, partial + (size_t)slice * N * (2 * NH), k, blockIdx.x, j0, j1, smem_raw);
+  const int slice = ATOM ? 0 : (CRED ? static_cast<int>(blockIdx.y) / ncl : static_cast<int>(blockIdx.y));
+  rtr_tile<L, R, C, CRED, ATOM>(N, pos, x, partial + (size_t)slice * N * (2 * NH), k, blockIdx.x, j0, j1,
+                                smem_raw);
 }
 
 // ---- batched form: one persistent launch over the tiles of many systems ----
@@ -1000,59 +1055,89 @@ int partial_cluster(int chunks, int maxcl) {
   }
 }
 
+// resident CTAs per SM of one reduction form of the per-context kernel (the
+// first call on each device sets its shared-memory limit there)
+template <int L, typename R, typename C, bool CRED, bool ATOM>
+int partial_form_occupancy() {
+  static PerDevice cache;
+  return cache.get(current_device, [] {
+    return kernel_setup(rtr_partial_kernel<L, R, C, CRED, ATOM>, C::BLOCK, Layout<L, R, C>::bytes);
+  });
+}
+
+// whether `atomic` asks for the in-L2 vector reduction of the partial sums
+// (FP32 only; otherwise the request is ignored)
+template <typename R>
+constexpr bool partial_atomic(bool atomic) {
+  return atomic && sizeof(R) == 4;
+}
+
+// partial-sum slices the epilogue must add after a launch with these options
 template <int L, typename R, typename C = Config<L, R>>
-int partial_cluster_occupancy() {
-  if constexpr (!C::ACC_SMEM) {
-    return 0;
+int partial_slices(int chunks, int maxcl, bool atomic) {
+  if (partial_atomic<R>(atomic)) return 1;
+  return chunks / partial_cluster<L, R, C>(chunks, maxcl);
+}
+
+template <int L, typename R, typename C, bool CRED, bool ATOM>
+cudaError_t launch_partial_form(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
+                                int ncl, cudaStream_t st) {
+  using LY = Layout<L, R, C>;
+  if (partial_form_occupancy<L, R, C, CRED, ATOM>() < 1) return cudaErrorInvalidConfiguration;
+  const int64_t chunk = (N + chunks - 1) / chunks;
+  dim3 grid(static_cast<unsigned>((N + C::BLOCK - 1) / C::BLOCK), static_cast<unsigned>(chunks));
+  if constexpr (ATOM) {
+    const cudaError_t e = cudaMemsetAsync(partial, 0, sizeof(Pair2<R>) * 2 * (L * (L + 2)) * N, st);
+    if (e != cudaSuccess) return e;
+  }
+  if constexpr (CRED) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(C::BLOCK);
+    cfg.dynamicSmemBytes = LY::bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = static_cast<unsigned>(ncl);
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, rtr_partial_kernel<L, R, C, true, ATOM>, static_cast<int>(N),
+                                             static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
+                                             static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk), ncl);
+    note_launch();
+    return e;
   } else {
-    static PerDevice cache;
-    return cache.get(current_device, [] {
-      return kernel_setup(rtr_partial_kernel<L, R, C, true>, C::BLOCK, Layout<L, R, C>::bytes);
-    });
+    rtr_partial_kernel<L, R, C, false, ATOM><<<grid, C::BLOCK, LY::bytes, st>>>(
+        static_cast<int>(N), static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
+        static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk), 1);
+    note_launch();
+    return cudaGetLastError();
   }
 }
 
 // `chunks` source chunks, partial-sum clusters of at most `maxcl` CTAs (1:
-// no cluster reduction); writes chunks / partial_cluster(chunks, maxcl)
-// partial slices (the count the epilogue must add)
+// no cluster reduction), `atomic`: all chunks added into one slice in L2
+// (FP32); writes partial_slices(chunks, maxcl, atomic) partial slices (the
+// count the epilogue must add)
 template <int L, typename R, typename C = Config<L, R>>
 cudaError_t launch_partial(int64_t N, const void* pos, const void* x, void* partial, double k, int chunks,
-                           cudaStream_t st, int maxcl = 1) {
-  using LY = Layout<L, R, C>;
+                           cudaStream_t st, int maxcl = 1, bool atomic = false) {
   const int occ = partial_occupancy<L, R, C>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (N <= 0) return cudaSuccess;
   if (chunks < 1) chunks = 1;
-  const int64_t chunk = (N + chunks - 1) / chunks;
-  dim3 grid(static_cast<unsigned>((N + C::BLOCK - 1) / C::BLOCK), static_cast<unsigned>(chunks));
   const int ncl = partial_cluster<L, R, C>(chunks, maxcl);
-  if constexpr (C::ACC_SMEM) {
-    if (ncl > 1) {
-      if (partial_cluster_occupancy<L, R, C>() < 1) return cudaErrorInvalidConfiguration;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = grid;
-      cfg.blockDim = dim3(C::BLOCK);
-      cfg.dynamicSmemBytes = LY::bytes;
-      cfg.stream = st;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 1;
-      at[0].val.clusterDim.y = static_cast<unsigned>(ncl);
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, rtr_partial_kernel<L, R, C, true>, static_cast<int>(N),
-                                               static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
-                                               static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk), ncl);
-      note_launch();
-      return e;
+  constexpr bool AT_OK = partial_atomic<R>(true);
+  if (ncl > 1) {
+    if constexpr (C::ACC_SMEM) {
+      if (AT_OK && atomic) return launch_partial_form<L, R, C, true, AT_OK>(N, pos, x, partial, k, chunks, ncl, st);
+      return launch_partial_form<L, R, C, true, false>(N, pos, x, partial, k, chunks, ncl, st);
     }
   }
-  rtr_partial_kernel<L, R, C, false><<<grid, C::BLOCK, LY::bytes, st>>>(
-      static_cast<int>(N), static_cast<const Pos4*>(pos), static_cast<const Pair2<R>*>(x),
-      static_cast<Pair2<R>*>(partial), k, static_cast<int>(chunk), 1);
-  note_launch();
-  return cudaGetLastError();
+  if (AT_OK && atomic) return launch_partial_form<L, R, C, false, AT_OK>(N, pos, x, partial, k, chunks, 1, st);
+  return launch_partial_form<L, R, C, false, false>(N, pos, x, partial, k, chunks, 1, st);
 }
 
 // persistent batched launch: one CTA per resident slot, tiles from `counter`

@@ -255,12 +255,12 @@ def test_preconditioner_apply_large_blocks(N, L, edge):
         B.celes_destroy(ctx)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("N,L,poly,n", CLUSTERS)
 def test_coupling_alternative_fp32_shape(N, L, poly, n, variant):
     # the autotuner's other FP32 launch shapes, forced, against the dense W:
-    # the alternative compile-time shape (1), the cluster reduction of the
-    # partial sums (2) and both (3)
+    # the alternative compile-time shape (bit 0), the cluster reduction of the
+    # partial sums (bit 1), their reduction in L2 (bit 2), and combinations
     sc = synth.random_cluster(23, N + L, N, L, radius=100.0, fill=0.25, n=n, polydisperse=poly)
     ctx = make_ctx(sc, variant=variant)
     try:
@@ -284,10 +284,13 @@ def test_coupling_alternative_fp32_shape(N, L, poly, n, variant):
         B.celes_destroy(ctx)
 
 
-@pytest.mark.parametrize("N,L,variant", [(333, 3, 2), (700, 4, 2), (700, 4, 3), (517, 5, 3), (450, 2, 2)])
+@pytest.mark.parametrize("N,L,variant", [(333, 3, 2), (700, 4, 2), (700, 4, 3), (517, 5, 3), (450, 2, 2),
+                                         (333, 3, 4), (700, 4, 4), (700, 4, 6), (517, 5, 5), (517, 5, 7),
+                                         (450, 2, 4), (450, 1, 6)])
 def test_coupling_cluster_reduction_on_sampled_rows(N, L, variant):
     # enough spheres for several source chunks per receiver block, so that the
-    # partial sums really are added in clusters of CTAs; ragged block counts
+    # partial sums really are added in clusters of CTAs or in L2; ragged block
+    # counts
     sc = synth.config2(0, N=N, lmax=L)
     ctx = make_ctx(sc, variant=variant)
     try:
@@ -317,7 +320,7 @@ def test_autotuner_picks_a_shape_and_keeps_the_result(L):
         y0 = gpu_matvec(c0, x, B.CELES_FP32)
         assert rel(y1, y0) < 1e-5
         v, ch, ms = B.celes_coupling_shape(c1, B.CELES_FP32)
-        assert v in (0, 1, 2, 3) and ch >= 1 and ms > 0
+        assert v in range(8) and ch >= 1 and ms > 0
         v0, ch0, ms0 = B.celes_coupling_shape(c0, B.CELES_FP32)
         assert v0 == 0 and ms0 == 0
         rows = [0, 700, sc.N - 1]
