@@ -182,16 +182,20 @@ def kernel_source_hash():
 
 def ncu_traffic(kernel_key, shape=None):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when it is absent, was taken on other kernel source, or on another
-    launch shape (variant, chunks) than `shape`."""
+    None when it is absent, was taken on other kernel source, or holds no
+    capture of the launch shape (variant, chunks) `shape`."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(kernel_key)
-        if shape is not None and e and (e.get("variant"), e.get("chunks")) != tuple(shape):
+        if not e or e.get("source_hash") != kernel_source_hash():
             return None
-        if e and e.get("source_hash") == kernel_source_hash():
+        if "shapes" in e:
+            if shape is None:
+                return None
+            return e["shapes"].get(f"{shape[0]},{shape[1]}", {}).get("dram_bytes_per_launch")
+        if shape is None or (e.get("variant"), e.get("chunks")) == tuple(shape):
             return e.get("dram_bytes_per_launch")
     except Exception:
         pass

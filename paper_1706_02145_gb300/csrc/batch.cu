@@ -189,14 +189,16 @@ __global__ void seg_combine_kernel(const VecSeg* __restrict__ seg, int m, int nv
 }
 
 // epilogue of the batched operator: y = x - T (W x) from the chunk partials
-// (grid: blocks x systems of one lmax group)
-template <typename R>
+// (grid: blocks x systems of one lmax group); ATOM: the one slice the
+// coupling launch added into, zeroed again after it is read (each element by
+// the thread that read it) for the next launch
+template <typename R, bool ATOM>
 __global__ void batch_epilogue_kernel(const BatchSys* __restrict__ sys) {
   const BatchSys S = sys[blockIdx.y];
   if (!S.active) return;
   const int L = S.L, NH = L * (L + 2);
   const long long total = (long long)S.N * NH;
-  const Pair2<R>* partial = static_cast<const Pair2<R>*>(S.partial);
+  Pair2<R>* partial = static_cast<Pair2<R>*>(S.partial);
   const Pair2<R>* x = static_cast<const Pair2<R>*>(S.x);
   const Pair2<R>* tq = static_cast<const Pair2<R>*>(S.tq);
   Pair2<R>* y = static_cast<Pair2<R>*>(S.y);
@@ -205,14 +207,18 @@ __global__ void batch_epilogue_kernel(const BatchSys* __restrict__ sys) {
     const long long i = t / NH;
     const int r = static_cast<int>(t - i * NH);
     R pr = 0, pi = 0, mr = 0, mi = 0;
-    for (int c = 0; c < S.chunks; ++c) {
-      const Pair2<R>* pc = partial + ((long long)c * S.N + i) * (2 * NH);
+    for (int c = 0; c < (ATOM ? 1 : S.chunks); ++c) {
+      Pair2<R>* pc = partial + ((long long)c * S.N + i) * (2 * NH);
       const Pair2<R> a = pc[r];
       const Pair2<R> b = pc[NH + r];
       pr += a.re;
       pi += a.im;
       mr += b.re;
       mi += b.im;
+      if (ATOM) {
+        pc[r] = Pair2<R>{0, 0};
+        pc[NH + r] = Pair2<R>{0, 0};
+      }
     }
     const Pair2<R> y1{static_cast<R>(0.5) * (pr + mr), static_cast<R>(0.5) * (pi + mi)};
     const Pair2<R> y2{static_cast<R>(0.5) * (pr - mr), static_cast<R>(0.5) * (pi - mi)};
@@ -319,7 +325,8 @@ struct System {
   int L, N, nmax;
   long long off;  // flat offset (complex elements)
   long long n;    // unknowns
-  int chunks, chunk;
+  int chunks, chunk;                 // FP64 source chunks (one partial slice each)
+  int chunks32, chunk32;             // FP32 source chunks (all added into one slice in L2)
   long long part_off32, part_off64;  // partial-sum offsets (bytes)
 };
 
@@ -408,10 +415,10 @@ int upload_descriptors(celes_batch* bt, int prec, const void* in, void* out) {
       b.tile0 = g.tile0[prec == 0 ? 1 : 0][q];
       b.N = S.N;
       b.L = S.L;
-      b.chunk = S.chunk;
+      b.chunk = prec == 0 ? S.chunk : S.chunk32;
       b.nrb = (S.N + rtr_rpb(S.L, prec == 0 ? CELES_FP64 : CELES_FP32) - 1) /
               rtr_rpb(S.L, prec == 0 ? CELES_FP64 : CELES_FP32);
-      b.chunks = S.chunks;
+      b.chunks = prec == 0 ? S.chunks : S.chunks32;
       b.active = bt->active[g.members[q]];
       d.push_back(b);
     }
@@ -456,9 +463,9 @@ int record_operator(celes_batch* bt, int prec) {
   for (const Group& g : bt->groups) {
     dim3 grid(64, static_cast<unsigned>(g.members.size()));
     if (prec == 0)
-      batch_epilogue_kernel<double><<<grid, 256, 0, bt->stream>>>(base + off);
+      batch_epilogue_kernel<double, false><<<grid, 256, 0, bt->stream>>>(base + off);
     else
-      batch_epilogue_kernel<float><<<grid, 256, 0, bt->stream>>>(base + off);
+      batch_epilogue_kernel<float, true><<<grid, 256, 0, bt->stream>>>(base + off);
     celes::note_launch();
     BK(cudaGetLastError(), "batched epilogue");
     off += g.members.size();
@@ -833,16 +840,26 @@ extern "C" int celes_batch_create(celes_batch** out, celes_ctx* const* ctxs, int
     const double want = work / (8.0 * std::max(1.0, slots) * rpb);
     int chunk = static_cast<int>(std::ceil(want / 32.0)) * 32;
     chunk = std::max(32, std::min(512, chunk));
+    // FP32: chunks cost no partial-sum traffic (one slice per system), so
+    // each system gets about two waves of tiles of its own, which keeps the
+    // GPU busy once only a few systems remain active
+    const int nrb_den = rpb > 0 ? rpb : 1;
     for (System& Sy : bt->sys)
       if (Sy.L == L) {
         Sy.chunk = std::min(Sy.N, chunk);
         Sy.chunks = (Sy.N + Sy.chunk - 1) / Sy.chunk;
+        const int nrb = (Sy.N + nrb_den - 1) / nrb_den;
+        const double ch32 = std::ceil(2.0 * std::max(1.0, slots) / nrb);
+        int c32 = static_cast<int>(std::ceil(Sy.N / ch32 / 32.0)) * 32;
+        c32 = std::max(64, std::min(chunk, c32));
+        Sy.chunk32 = std::min(Sy.N, c32);
+        Sy.chunks32 = (Sy.N + Sy.chunk32 - 1) / Sy.chunk32;
       }
   }
   for (System& Sy : bt->sys) {
     Sy.part_off32 = p32;
     Sy.part_off64 = p64;
-    p32 += (long long)Sy.chunks * Sy.n * 8;
+    p32 += (long long)Sy.n * 8;
     p64 += (long long)Sy.chunks * Sy.n * 16;
   }
   bt->ntot = off;
@@ -855,7 +872,7 @@ extern "C" int celes_batch_create(celes_batch** out, celes_ctx* const* ctxs, int
       for (int p = 0; p < 2; ++p) {
         const int rpb = rtr_rpb(L, p == 0 ? CELES_FP32 : CELES_FP64);
         g.tile0[p].push_back(g.ntiles[p]);
-        g.ntiles[p] += (long long)((bt->sys[s].N + rpb - 1) / rpb) * bt->sys[s].chunks;
+        g.ntiles[p] += (long long)((bt->sys[s].N + rpb - 1) / rpb) * (p == 0 ? bt->sys[s].chunks32 : bt->sys[s].chunks);
       }
     }
     if (!g.members.empty()) bt->groups.push_back(std::move(g));
@@ -878,6 +895,8 @@ extern "C" int celes_batch_create(celes_batch** out, celes_ctx* const* ctxs, int
       !ok(bt->hdots.ensure(S * (m + 2) * 16))) {
     return CELES_ENOMEM;
   }
+  // the FP32 partial slices start at zero; each batched epilogue leaves them so
+  if (p32 > 0 && !ok(cudaMemsetAsync(bt->part32.p, 0, static_cast<size_t>(p32), bt->stream))) return CELES_ECUDA;
   // T a of every system into the flat vector
   for (const System& Sy : bt->sys) {
     const celes::CtxView& v = bt->view[Sy.e];

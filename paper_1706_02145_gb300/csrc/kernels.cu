@@ -212,55 +212,92 @@ cudaError_t launch_plane_wave(int64_t N, int L, double k, const void* pos, doubl
 //        + 2 pi e^{+i aG} i^{|m+1|} e^{-i(m+1) phi_G} J_{|m+1|}(k rho_G sin) (d_j1 + i d_j2)/2
 // (rho_G, phi_G, z_G) cylindrical coordinates of r_i - r_G.  beta integral by
 // the Gauss-Legendre nodes/weights given in (nodes, weights).
-__global__ void gaussian_beam_kernel(int64_t N, int L, double k, const Pos4* __restrict__ pos, double w,
-                                     double fx, double fy, double fz, double alphaG, double e0r, double e0i, int nb,
-                                     const double* __restrict__ nodes, const double* __restrict__ weights,
-                                     double* __restrict__ a) {
+// One CTA per sphere; its threads take the beta nodes.  Per node a thread
+// forms what all rows of the sphere share (the Gaussian weight, e^{i k z_G
+// cos}, J_mu(k rho_G sin) for mu = 0..L+1 and pi/tau for every |m|), then adds
+// each row's term; the terms of a row are summed over the warp by shuffles and
+// over the warps in shared memory.
+constexpr int kGbThreads = 128;
+constexpr int kGbMaxL = 5;
+constexpr int kGbMaxRows = 2 * kGbMaxL * (kGbMaxL + 2);
+
+__global__ void __launch_bounds__(kGbThreads)
+    gaussian_beam_kernel(int64_t N, int L, double k, const Pos4* __restrict__ pos, double w, double fx, double fy,
+                         double fz, double alphaG, double e0r, double e0i, int nb, const double* __restrict__ nodes,
+                         const double* __restrict__ weights, double* __restrict__ a) {
+  __shared__ cd sU[2 * kGbMaxL + 1], sV[2 * kGbMaxL + 1];
+  __shared__ double red[kGbThreads / 32][kGbMaxRows][2];
   const int nmax = 2 * L * (L + 2);
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= N * nmax) return;
-  const int64_t i = t / nmax;
-  const int n = static_cast<int>(t - i * nmax);
-  int tau, l, m;
-  row_decode(n, L, tau, l, m);
-  const int am = m < 0 ? -m : m;
+  const int64_t i = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const Pos4 r = pos[i];
   const double dx = r.x - fx, dy = r.y - fy, dz = r.z - fz;
   const double rho = sqrt(dx * dx + dy * dy);
   const double phiG = atan2(dy, dx);
-  const cd Um = cexp_i(-alphaG - (m - 1) * phiG) * ipow(abs(m - 1));
-  const cd Vm = cexp_i(alphaG - (m + 1) * phiG) * ipow(abs(m + 1));
-  cd acc = mkc(0.0);
-  double pi[16], ta[16];
-  for (int q = 0; q < nb; ++q) {
-    const double b = nodes[q];
-    double sb, cb;
-    sincos(b, &sb, &cb);
-    const double gw = weights[q] * sb * cb * exp(-0.25 * (w * k * sb) * (w * k * sb));
-    if (gw == 0.0) continue;
-    pi_tau_m(L, am, cb, sb, pi, ta);
-    const double xr = k * rho * sb;
-    const double Jm = jn(abs(m - 1), xr);
-    const double Jp = jn(abs(m + 1), xr);
-    // I_1 = pi (U + V), I_2 = pi (-i U + i V), U = Um Jm, V = Vm Jp (2 pi * 1/2 = pi)
-    const cd U = Jm * Um, V = Jp * Vm;
-    const cd I1 = 3.14159265358979323846 * (U + V);
-    const cd I2 = 3.14159265358979323846 * (cd{0, -1} * U + cd{0, 1} * V);
-    const cd B1 = b_transform(tau, l, m, 1, pi[l], ta[l], true);
-    const cd B2 = b_transform(tau, l, m, 2, pi[l], ta[l], true);
-    acc = acc + (gw * cexp_i(k * dz * cb)) * (B1 * I1 + B2 * I2);
+  if (tid <= 2 * L) {
+    const int m = tid - L;
+    sU[tid] = cexp_i(-alphaG - (m - 1) * phiG) * ipow(abs(m - 1));
+    sV[tid] = cexp_i(alphaG - (m + 1) * phiG) * ipow(abs(m + 1));
   }
-  const cd v = (k * k * w * w / 3.14159265358979323846) * (mkc(e0r, e0i) * acc);
-  a[2 * t] = v.re;
-  a[2 * t + 1] = v.im;
+  for (int q = tid; q < (kGbThreads / 32) * kGbMaxRows * 2; q += blockDim.x) (&red[0][0][0])[q] = 0.0;
+  __syncthreads();
+  for (int q0 = 0; q0 < nb; q0 += blockDim.x) {
+    const int q = q0 + tid;
+    double gw = 0.0, sb = 0.0, cb = 1.0;
+    if (q < nb) {
+      sincos(nodes[q], &sb, &cb);
+      gw = weights[q] * sb * cb * exp(-0.25 * (w * k * sb) * (w * k * sb));
+    }
+    const bool live = gw != 0.0;
+    double J[kGbMaxL + 2];
+    double pi_all[kGbMaxL + 1][kGbMaxL + 1], ta_all[kGbMaxL + 1][kGbMaxL + 1];
+    cd ez = mkc(0.0);
+    if (live) {
+      const double xr = k * rho * sb;
+      for (int mu = 0; mu <= L + 1; ++mu) J[mu] = jn(mu, xr);
+      for (int am = 0; am <= L; ++am) pi_tau_m(L, am, cb, sb, pi_all[am], ta_all[am]);
+      ez = gw * cexp_i(k * dz * cb);
+    }
+    for (int n = 0; n < nmax; ++n) {
+      cd c = mkc(0.0);
+      if (live) {
+        int tau, l, m;
+        row_decode(n, L, tau, l, m);
+        const int am = m < 0 ? -m : m;
+        // I_1 = pi (U + V), I_2 = pi (-i U + i V), U = Um J_|m-1|, V = Vm J_|m+1| (2 pi * 1/2 = pi)
+        const cd U = J[abs(m - 1)] * sU[m + L], V = J[abs(m + 1)] * sV[m + L];
+        const cd I1 = 3.14159265358979323846 * (U + V);
+        const cd I2 = 3.14159265358979323846 * (cd{0, -1} * U + cd{0, 1} * V);
+        const cd B1 = b_transform(tau, l, m, 1, pi_all[am][l], ta_all[am][l], true);
+        const cd B2 = b_transform(tau, l, m, 2, pi_all[am][l], ta_all[am][l], true);
+        c = ez * (B1 * I1 + B2 * I2);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        c.re += __shfl_down_sync(0xffffffffu, c.re, o);
+        c.im += __shfl_down_sync(0xffffffffu, c.im, o);
+      }
+      if (lane == 0) {
+        red[wid][n][0] += c.re;
+        red[wid][n][1] += c.im;
+      }
+    }
+  }
+  __syncthreads();
+  for (int n = tid; n < nmax; n += blockDim.x) {
+    cd acc = mkc(0.0);
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) acc = acc + cd{red[q][n][0], red[q][n][1]};
+    const cd v = (k * k * w * w / 3.14159265358979323846) * (mkc(e0r, e0i) * acc);
+    a[2 * (i * nmax + n)] = v.re;
+    a[2 * (i * nmax + n) + 1] = v.im;
+  }
 }
 
 cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, double w, const double* focus,
                                  double alphaG, double e0r, double e0i, int nb, const double* nodes,
                                  const double* weights, double* a, cudaStream_t st) {
-  const int64_t total = N * 2 * L * (L + 2);
-  const int threads = 128;
-  gaussian_beam_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, st>>>(
+  if (L < 1 || L > kGbMaxL) return cudaErrorInvalidValue;
+  if (N <= 0) return cudaSuccess;
+  gaussian_beam_kernel<<<static_cast<unsigned>(N), kGbThreads, 0, st>>>(
       N, L, k, static_cast<const Pos4*>(pos), w, focus[0], focus[1], focus[2], alphaG, e0r, e0i, nb, nodes, weights,
       a);
   note_launch();

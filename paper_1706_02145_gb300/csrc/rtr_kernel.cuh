@@ -744,6 +744,13 @@ struct Layout {
   static constexpr size_t bytes = off_xy + (C::XY_SMEM ? (C::XY_INPLACE ? 1 : 2) * col : 0);
 };
 
+// whether `atomic` asks for the in-L2 vector reduction of the partial sums
+// (FP32 only; otherwise the request is ignored)
+template <typename R>
+constexpr bool partial_atomic(bool atomic) {
+  return atomic && sizeof(R) == 4;
+}
+
 // One tile: receivers rb*BLOCK .. +BLOCK against sources j0 .. j1 - 1; writes
 // this tile's partial sums in the +- basis to out ([N][2][NH] complex, the
 // slice of the tile's source chunk).  Called by every thread of the CTA.
@@ -963,7 +970,10 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
 // lmax in one launch).  Its tiles are (receiver block, source chunk) pairs
 // numbered tile0 .. tile0 + nrb * chunks - 1 within the launch; CTAs take
 // tiles from a global counter (dynamic scheduling, so uneven ensembles
-// balance), and systems whose flag `active` is 0 are skipped.
+// balance), and systems whose flag `active` is 0 are skipped.  The FP32
+// launch adds all chunks of a system into its one partial slice in L2 (the
+// batched epilogue reads the slice and zeroes it again); the FP64 launch
+// writes one slice per chunk.
 struct BatchSys {
   const Pos4* pos;
   const void* x;      // input vector [N][nmax] complex (FP32 or FP64 as launched)
@@ -975,7 +985,7 @@ struct BatchSys {
   int N, L, chunk, nrb, chunks, active;
 };
 
-template <int L, typename R, typename C = Config<L, R>>
+template <int L, typename R, typename C = Config<L, R>, bool ATOM = partial_atomic<R>(true)>
 __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     rtr_batch_kernel(const BatchSys* __restrict__ sys, int nsys, long long ntiles,
                      unsigned long long* __restrict__ counter) {
@@ -1002,9 +1012,9 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     if (ch >= S.chunks) continue;  // never taken with consistent descriptors
     const int j0 = ch * S.chunk;
     const int j1 = min(S.N, j0 + S.chunk);
-    rtr_tile<L, R, C>(S.N, S.pos, static_cast<const Pair2<R>*>(S.x),
-                      static_cast<Pair2<R>*>(S.partial) + (size_t)ch * S.N * (2 * NH), S.k, rb, j0, j1,
-                      smem_raw);
+    rtr_tile<L, R, C, false, ATOM>(S.N, S.pos, static_cast<const Pair2<R>*>(S.x),
+                                   static_cast<Pair2<R>*>(S.partial) + (ATOM ? 0 : (size_t)ch * S.N * (2 * NH)), S.k,
+                                   rb, j0, j1, smem_raw);
   }
 }
 
@@ -1063,13 +1073,6 @@ int partial_form_occupancy() {
   return cache.get(current_device, [] {
     return kernel_setup(rtr_partial_kernel<L, R, C, CRED, ATOM>, C::BLOCK, Layout<L, R, C>::bytes);
   });
-}
-
-// whether `atomic` asks for the in-L2 vector reduction of the partial sums
-// (FP32 only; otherwise the request is ignored)
-template <typename R>
-constexpr bool partial_atomic(bool atomic) {
-  return atomic && sizeof(R) == 4;
 }
 
 // partial-sum slices the epilogue must add after a launch with these options
