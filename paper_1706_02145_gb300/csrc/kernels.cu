@@ -309,13 +309,19 @@ cudaError_t launch_gaussian_beam(int64_t N, int L, double k, const void* pos, do
 // ---------------------------------------------------------------------------
 constexpr int kVecThreads = 256;
 
-// partial[b][j] = sum over this block's range of conj(V_j) w, eight vectors per
-// pass (w read once per pass); per-thread and warp sums in the vector's own
-// precision (a handful of terms each), block sums in FP64
+// partial[b][j] = sum over this block's range of conj(V_j) w, sixteen vectors
+// per pass (w read once per pass), two elements per loop step so that 34
+// loads are in flight per thread; per-thread and warp sums in the vector's own
+// precision (a few dozen terms each), block sums in FP64.  Launched with two
+// CTAs per SM (vec_dot_blocks): each thread then covers enough elements per
+// pass to repay the pass's reduction (measured on GB300 at 480 000 elements
+// and 50 vectors: 62 us against 118 us for eight vectors per pass at four
+// CTAs per SM).
 template <typename R>
-__global__ void multi_dotc_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V, int64_t ldv,
-                                  const Pair2<R>* __restrict__ w, double* __restrict__ partial) {
-  constexpr int JT = 8;
+__global__ void __launch_bounds__(kVecThreads) multi_dotc_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V,
+                                                                int64_t ldv, const Pair2<R>* __restrict__ w,
+                                                                double* __restrict__ partial) {
+  constexpr int JT = 16;
   __shared__ double red[2 * JT][kVecThreads / 32];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int j0 = 0; j0 < nv; j0 += JT) {
@@ -323,14 +329,29 @@ __global__ void multi_dotc_kernel(int64_t n, int nv, const Pair2<R>* __restrict_
     R sr[JT], si[JT];
 #pragma unroll
     for (int q = 0; q < JT; ++q) sr[q] = si[q] = static_cast<R>(0);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
-      const Pair2<R> b = w[t];
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; t + stride < n; t += 2 * stride) {
+      const Pair2<R> b0 = w[t], b1 = w[t + stride];
 #pragma unroll
       for (int q = 0; q < JT; ++q) {
         if (q < nj) {
-          const Pair2<R> a = V[(j0 + q) * ldv + t];
-          sr[q] = fma_(a.re, b.re, fma_(a.im, b.im, sr[q]));
-          si[q] = fma_(a.re, b.im, fma_(-a.im, b.re, si[q]));
+          const Pair2<R> a0 = V[(j0 + q) * ldv + t];
+          const Pair2<R> a1 = V[(j0 + q) * ldv + t + stride];
+          sr[q] = fma_(a0.re, b0.re, fma_(a0.im, b0.im, sr[q]));
+          si[q] = fma_(a0.re, b0.im, fma_(-a0.im, b0.re, si[q]));
+          sr[q] = fma_(a1.re, b1.re, fma_(a1.im, b1.im, sr[q]));
+          si[q] = fma_(a1.re, b1.im, fma_(-a1.im, b1.re, si[q]));
+        }
+      }
+    }
+    if (t < n) {
+      const Pair2<R> b0 = w[t];
+#pragma unroll
+      for (int q = 0; q < JT; ++q) {
+        if (q < nj) {
+          const Pair2<R> a0 = V[(j0 + q) * ldv + t];
+          sr[q] = fma_(a0.re, b0.re, fma_(a0.im, b0.im, sr[q]));
+          si[q] = fma_(a0.re, b0.im, fma_(-a0.im, b0.re, si[q]));
         }
       }
     }
@@ -399,7 +420,7 @@ int device_sms() {
 
 int vec_dot_blocks(int64_t n) {
   const int64_t b = (n + kVecThreads - 1) / kVecThreads;
-  const int64_t cap = 4LL * device_sms();
+  const int64_t cap = 2LL * device_sms();
   return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
@@ -419,23 +440,56 @@ template cudaError_t launch_multi_dotc<double>(int64_t, int, const void*, int64_
                                                cudaStream_t);
 
 // w <- alpha0 * w - sum_j h_j V_j   (h given as FP64 complex on the device;
-// arithmetic in the vector's precision)
+// arithmetic in the vector's precision).  Two elements
+// per thread step and the loads of eight vectors issued before their FMAs
+// (16 loads in flight per thread), four CTAs per SM; each element's sum is
+// formed in the same order as a plain loop over j (measured on GB300 at
+// 480 000 elements and 50 vectors: 70 us against 110 us for one element and
+// one vector at a time).
 template <typename R>
-__global__ void multi_axpy_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V, int64_t ldv,
-                                  const double* __restrict__ h, double alpha0, Pair2<R>* __restrict__ w) {
+__global__ void __launch_bounds__(kVecThreads) multi_axpy_kernel(int64_t n, int nv, const Pair2<R>* __restrict__ V,
+                                                                int64_t ldv, const double* __restrict__ h,
+                                                                double alpha0, Pair2<R>* __restrict__ w) {
+  constexpr int U = 8;
   __shared__ R hs[2 * 128];
   for (int q = threadIdx.x; q < 2 * nv && q < 256; q += blockDim.x) hs[q] = static_cast<R>(h[q]);
   __syncthreads();
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    R ar = static_cast<R>(alpha0) * w[t].re, ai = static_cast<R>(alpha0) * w[t].im;
-    for (int j = 0; j < nv; ++j) {
-      const Pair2<R> v = V[j * ldv + t];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += 2 * stride) {
+    const bool two = t + stride < n;
+    const int64_t t1 = two ? t + stride : t;
+    R ar0 = static_cast<R>(alpha0) * w[t].re, ai0 = static_cast<R>(alpha0) * w[t].im;
+    R ar1 = static_cast<R>(alpha0) * w[t1].re, ai1 = static_cast<R>(alpha0) * w[t1].im;
+    int j = 0;
+    for (; j + U <= nv; j += U) {
+      Pair2<R> v0[U], v1[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        v0[u] = V[(j + u) * ldv + t];
+        v1[u] = V[(j + u) * ldv + t1];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int jj = j + u;
+        const R hr = jj < 128 ? hs[2 * jj] : static_cast<R>(h[2 * jj]);
+        const R hi = jj < 128 ? hs[2 * jj + 1] : static_cast<R>(h[2 * jj + 1]);
+        ar0 = fma_(-hr, v0[u].re, fma_(hi, v0[u].im, ar0));
+        ai0 = fma_(-hr, v0[u].im, fma_(-hi, v0[u].re, ai0));
+        ar1 = fma_(-hr, v1[u].re, fma_(hi, v1[u].im, ar1));
+        ai1 = fma_(-hr, v1[u].im, fma_(-hi, v1[u].re, ai1));
+      }
+    }
+    for (; j < nv; ++j) {
+      const Pair2<R> a = V[j * ldv + t], b = V[j * ldv + t1];
       const R hr = j < 128 ? hs[2 * j] : static_cast<R>(h[2 * j]);
       const R hi = j < 128 ? hs[2 * j + 1] : static_cast<R>(h[2 * j + 1]);
-      ar = fma_(-hr, v.re, fma_(hi, v.im, ar));
-      ai = fma_(-hr, v.im, fma_(-hi, v.re, ai));
+      ar0 = fma_(-hr, a.re, fma_(hi, a.im, ar0));
+      ai0 = fma_(-hr, a.im, fma_(-hi, a.re, ai0));
+      ar1 = fma_(-hr, b.re, fma_(hi, b.im, ar1));
+      ai1 = fma_(-hr, b.im, fma_(-hi, b.re, ai1));
     }
-    w[t] = Pair2<R>{ar, ai};
+    w[t] = Pair2<R>{ar0, ai0};
+    if (two) w[t1] = Pair2<R>{ar1, ai1};
   }
 }
 
@@ -468,7 +522,10 @@ static int vec_grid(int64_t n) {
 template <typename R>
 cudaError_t launch_multi_axpy(int64_t n, int nv, const void* V, int64_t ldv, const double* h, double alpha0, void* w,
                               cudaStream_t st) {
-  multi_axpy_kernel<R><<<vec_grid(n), kVecThreads, 0, st>>>(n, nv, static_cast<const Pair2<R>*>(V), ldv, h, alpha0,
+  const int64_t pairs = (n + 2 * kVecThreads - 1) / (2 * kVecThreads);
+  const int64_t cap = 4LL * device_sms();
+  const unsigned grid = static_cast<unsigned>(pairs < cap ? (pairs > 0 ? pairs : 1) : cap);
+  multi_axpy_kernel<R><<<grid, kVecThreads, 0, st>>>(n, nv, static_cast<const Pair2<R>*>(V), ldv, h, alpha0,
                                                             static_cast<Pair2<R>*>(w));
   note_launch();
   return cudaGetLastError();
