@@ -68,7 +68,10 @@ struct VecSeg {
 
 // ---- segmented vector kernels (grid: kSegBlocks x systems) ----------------
 
-// partial[s][b][j] = sum over block b's share of system s of conj(V_j) w
+// partial[s][b][j] = sum over block b's share of system s of conj(V_j) w;
+// per-thread and warp sums in the vector's own precision (at most a few dozen
+// terms each: the FP64 pipe runs at 1/64 of the FP32 rate on this part), block
+// sums in FP64
 template <typename R>
 __global__ void seg_dotc_kernel(const VecSeg* __restrict__ seg, int nv, const Pair2<R>* __restrict__ V,
                                 long long ldv, const Pair2<R>* __restrict__ w, double* __restrict__ partial) {
@@ -77,9 +80,9 @@ __global__ void seg_dotc_kernel(const VecSeg* __restrict__ seg, int nv, const Pa
   __shared__ double red[2 * kDotJ][kSegThreads / 32];
   for (int j0 = 0; j0 < nv; j0 += kDotJ) {
     const int nj = nv - j0 < kDotJ ? nv - j0 : kDotJ;
-    double sr[kDotJ], si[kDotJ];
+    R sr[kDotJ], si[kDotJ];
 #pragma unroll
-    for (int q = 0; q < kDotJ; ++q) sr[q] = si[q] = 0.0;
+    for (int q = 0; q < kDotJ; ++q) sr[q] = si[q] = static_cast<R>(0);
     if (S.active) {
       for (int t = blockIdx.x * kSegThreads + threadIdx.x; t < S.n; t += kSegBlocks * kSegThreads) {
         const Pair2<R> b = w[S.off + t];
@@ -87,22 +90,22 @@ __global__ void seg_dotc_kernel(const VecSeg* __restrict__ seg, int nv, const Pa
         for (int q = 0; q < kDotJ; ++q) {
           if (q < nj) {
             const Pair2<R> a = V[(j0 + q) * ldv + S.off + t];
-            sr[q] += static_cast<double>(a.re) * b.re + static_cast<double>(a.im) * b.im;
-            si[q] += static_cast<double>(a.re) * b.im - static_cast<double>(a.im) * b.re;
+            sr[q] = celes::fma_(a.re, b.re, celes::fma_(a.im, b.im, sr[q]));
+            si[q] = celes::fma_(a.re, b.im, celes::fma_(-a.im, b.re, si[q]));
           }
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < kDotJ; ++q) {
-      double a = sr[q], b = si[q];
+      R a = sr[q], b = si[q];
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
         b += __shfl_down_sync(0xffffffffu, b, o);
       }
       if ((threadIdx.x & 31) == 0) {
-        red[2 * q][threadIdx.x >> 5] = a;
-        red[2 * q + 1][threadIdx.x >> 5] = b;
+        red[2 * q][threadIdx.x >> 5] = static_cast<double>(a);
+        red[2 * q + 1][threadIdx.x >> 5] = static_cast<double>(b);
       }
     }
     __syncthreads();
@@ -138,9 +141,22 @@ __global__ void seg_axpy_kernel(const VecSeg* __restrict__ seg, int nv, const Pa
   const VecSeg S = seg[s];
   if (!S.active) return;
   const double* hs = h + (long long)s * nv * 2;
+  constexpr int U = 8;  // basis vectors whose loads are issued before their FMAs
   for (int t = blockIdx.x * kSegThreads + threadIdx.x; t < S.n; t += kSegBlocks * kSegThreads) {
     R ar = w[S.off + t].re, ai = w[S.off + t].im;
-    for (int j = 0; j < nv; ++j) {
+    int j = 0;
+    for (; j + U <= nv; j += U) {
+      Pair2<R> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = V[(j + u) * ldv + S.off + t];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const R hr = static_cast<R>(hs[2 * (j + u)]), hi = static_cast<R>(hs[2 * (j + u) + 1]);
+        ar = celes::fma_(-hr, v[u].re, celes::fma_(hi, v[u].im, ar));
+        ai = celes::fma_(-hr, v[u].im, celes::fma_(-hi, v[u].re, ai));
+      }
+    }
+    for (; j < nv; ++j) {
       const Pair2<R> v = V[j * ldv + S.off + t];
       const R hr = static_cast<R>(hs[2 * j]), hi = static_cast<R>(hs[2 * j + 1]);
       ar = celes::fma_(-hr, v.re, celes::fma_(hi, v.im, ar));
