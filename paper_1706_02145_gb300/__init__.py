@@ -38,13 +38,17 @@ class Simulation:
 
     positions (N, 3), radii (N,), n_sphere (N,) complex refractive indices,
     n0 background index, wavelength (vacuum, same length unit), lmax.
+    autotune / variant: the coupling kernel's launch shape (celes_options);
+    autotune=False gives bit-reproducible FP32 products.
     """
 
-    def __init__(self, positions, radii, n_sphere, n0, wavelength, lmax, device=0, check_overlap=True, chunks=0):
+    def __init__(self, positions, radii, n_sphere, n0, wavelength, lmax, device=0, check_overlap=True, chunks=0,
+                 autotune=True, variant=-1):
         import numpy as np
         self.k0 = 2.0 * np.pi / wavelength
         self.ctx = binding.celes_create(positions, radii, n_sphere, n0, self.k0, lmax, device=device,
-                                        check_overlap=check_overlap, chunks=chunks)
+                                        check_overlap=check_overlap, chunks=chunks, autotune=autotune,
+                                        variant=variant)
         self.lmax = lmax
         self.N = binding.celes_num_spheres(self.ctx)
         self.nmax = binding.celes_nmax(self.ctx)
